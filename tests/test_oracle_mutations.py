@@ -1,0 +1,114 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that its pins
+catch every one: a dropped term, a wrong sign, a wrong conjugation, a wrong
+normalisation, a transposed operand."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense as Dn
+from oracle import tetra as T
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+E = T.strain_tensor_from_voigt([1e-3, -2e-4, 5e-4, 3e-4, -1e-4, 2e-3])
+
+
+def _pins_hold():
+    rows = np.loadtxt(os.path.join(GOLDEN, "dq_special_points.txt"))
+    for row in rows:
+        D = T.D_at(*(np.array(v) for v in row[:3] * np.pi))
+        if not np.allclose(D, row[3::2] + 1j * row[4::2], atol=1e-12):
+            return False
+    grid = (4, 4, 4)
+    ids = synth.random_phase_map(grid, 3, seed=1)
+    table = np.stack([synth.isotropic_voigt(1.0, 0.3), synth.isotropic_voigt(10.0, 0.25),
+                      synth.isotropic_voigt(0.0, 0.3)])
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((6, 6))
+    lam0 = T.stiffness_tensor(A @ A.T + 30 * np.eye(6))
+    seen = []
+    try:
+        T.solve_alg1(ids, table, lam0, E, tol=0, max_iter=3,
+                     callback=lambda n, e, d1, d2, sm: seen.append((e, d1.copy(), d2.copy())))
+    except Exception:
+        return False
+    P = Dn.DenseProblem(ids, table, lam0)
+    for n, u in enumerate(P.richardson(E, 3)):
+        d1, d2, _, _ = P.fields(u, E)
+        err, _ = P.error(u, E)
+        if not (np.allclose(seen[n][1], d1, atol=1e-14) and np.allclose(seen[n][2], d2, atol=1e-14)
+                and abs(seen[n][0] - err) <= 1e-9 * err):
+            return False
+    return True
+
+
+def test_pins_hold_unmutated():
+    assert _pins_hold()
+
+
+def _mut_D_sign(orig):
+    def D_at(q1, q2, q3):
+        D = orig(q1, q2, q3).copy()
+        D[1] = 0.5 * (np.exp(0.5j * (q1 + q2 + q3)) - np.exp(0.5j * (q1 - q2 - q3))
+                      + np.exp(0.5j * (-q1 + q2 - q3)) + np.exp(0.5j * (-q1 - q2 + q3)))
+        return D
+    return D_at
+
+
+def _mut_drop_T2(orig):
+    def evaluate(u_q, D, mat, eps_bar, grid, workers=None):
+        d1, d2, s1, s2, f, L2, sm = orig(u_q, D, mat, eps_bar, grid, workers)
+        s1q = T.ft(s1)
+        f = np.einsum("ji...,i...->j...", s1q, np.conj(D))
+        return d1, d2, s1, s2, f, L2, sm
+    return evaluate
+
+
+def _mut_conj_T1(orig):
+    def sym_outer(a, b):
+        return orig(np.conj(a), b)
+    return sym_outer
+
+
+def _mut_ift_norm(orig):
+    def ift(field_q, grid, workers=None):
+        return orig(field_q, grid, workers) / np.prod(grid)
+    return ift
+
+
+def _mut_L2_factor(orig):
+    def evaluate(u_q, D, mat, eps_bar, grid, workers=None):
+        out = list(orig(u_q, D, mat, eps_bar, grid, workers))
+        out[5] = 2 * out[5]
+        return tuple(out)
+    return evaluate
+
+
+def _mut_green_transpose(orig):
+    def green(D, lam0, grid, half=True):
+        Om = orig(D, lam0, grid, half)
+        # transposed operand in the contraction with lambda0 (j <-> i) is invisible
+        # for symmetric tensors, so plant the non-symmetric analogue: drop the
+        # second term of Eq. (Green_tensor)
+        A = np.einsum("i...,jikl,k...->jl...", np.conj(D), lam0, D).real
+        mask = T.translation_modes(grid, half)
+        A = np.moveaxis(A, (0, 1), (-2, -1)).copy()
+        A[mask] = np.eye(3)
+        Om2 = np.linalg.inv(A)
+        Om2[mask] = 0
+        return np.moveaxis(Om2, (-2, -1), (0, 1))
+    return green
+
+
+@pytest.mark.parametrize("name,factory", [
+    ("D_at", _mut_D_sign),
+    ("evaluate", _mut_drop_T2),
+    ("sym_outer", _mut_conj_T1),
+    ("ift", _mut_ift_norm),
+    ("evaluate", _mut_L2_factor),
+    ("green", _mut_green_transpose),
+])
+def test_planted_mistake_is_caught(monkeypatch, name, factory):
+    monkeypatch.setattr(T, name, factory(getattr(T, name)))
+    assert not _pins_hold()
