@@ -1,0 +1,165 @@
+/*
+ * hs.h -- C ABI of the tetrahedral-stencil FFT homogenization solver for
+ * GB300 (sm_103a).
+ *
+ * The solver computes the discrete mechanical equilibrium of a periodic 3D
+ * voxel microstructure under an applied macroscopic strain, with the
+ * tetrahedral stencil of Finel, "A fast and robust discrete FFT-based solver
+ * for computational homogenization" (arXiv 2405.11168), and iterates the
+ * displacement-based basic scheme of its Algorithm 1 (Section 2.6):
+ *
+ *   deps^T1 = D (x)_s u,  deps^T2 = -conj(D) (x)_s u          (Eq. deps_dep_Q)
+ *   sigma^T = lambda(r) : (E + deps^T(r))                       (Algorithm 1 step 3)
+ *   u(q) <- u(q) - Omega(q).{sigma^T1(q).conj(D) - sigma^T2(q).D}  (Eq. basic_scheme_dep_2)
+ *   err  = L2 / ||<sigma>||, stop when err < tol                 (Eqs. L2-norm, tolerance)
+ *   eps = E + 1/2 (deps^T1 + deps^T2), sigma = 1/2 (sigma^T1 + sigma^T2)  (Eq. final_fields)
+ *
+ * Conventions used by every entry point:
+ *  - grid[3] = {N1, N2, N3}; real fields are row-major [N3][N2][N1] (x fastest).
+ *  - Voigt order 11, 22, 33, 23, 13, 12.  Strains passed in and returned are
+ *    TENSOR components (E[3] = eps_23, not gamma_23).  Stiffness matrices are
+ *    the engineering 6x6 Voigt matrices (sigma_V = C eps_V with doubled shear
+ *    strains), so the tensor components lambda_ijkl equal the Voigt entries.
+ *  - Units are the caller's; err is dimensionless.
+ *  - Every call runs on the CUDA stream given to hs_create and returns after
+ *    the results it reports are on the host.
+ *  - Errors are negative hs_status values; on error nothing is written to the
+ *    caller's outputs.  No entry point aborts or traps.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hs_ctx hs_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  HS_OK = 0,
+  HS_NOT_CONVERGED = 1,        /* max_iter reached; outputs hold the last iterate */
+  HS_ERR_INVALID_ARG = -1,     /* bad pointer, size, material, tolerance or load */
+  HS_ERR_UNSUPPORTED_SIZE = -2,/* N_i odd, < 4, > 512, or with a prime factor other than 2, 3 */
+  HS_ERR_OOM = -3,             /* the workspace given is smaller than hs_workspace_size() */
+  HS_ERR_CUDA = -4,            /* a CUDA call failed (see hs_last_error) */
+  HS_DIVERGED = -5,            /* err became NaN/Inf or grew 1e6x above its minimum */
+  HS_ERR_TIMEOUT = -6          /* reserved: a bounded device wait gave up */
+} hs_status;
+
+enum { HS_FP64 = 0, HS_FP32 = 1, HS_FP32_REFINED = 2 };
+enum { HS_IDS_U8 = 0, HS_IDS_U16 = 1 };
+
+/* Microstructure: a phase id per voxel and a stiffness per phase
+ * (lambda(r) of Eq. linear_elasticity, with eps0 = 0). */
+typedef struct {
+  int kind;             /* HS_IDS_U8 or HS_IDS_U16 */
+  const void* ids;      /* [N3][N2][N1] phase ids; host or device pointer, read during hs_create only */
+  const double* table;  /* host pointer, nphase x 36: row-major 6x6 Voigt stiffness per phase;
+                           must be symmetric with a non-negative diagonal (C = 0 is a void) */
+  int nphase;           /* 1..65536; every id must be < nphase */
+} hs_material;
+
+typedef struct {
+  int precision;        /* HS_FP64, HS_FP32 or HS_FP32_REFINED */
+  int check_every;      /* host polls convergence every this many iterations (>= 1) */
+  int out_f32;          /* field outputs as float (1) or double (0) */
+  int inner_max;        /* HS_FP32_REFINED: max FP32 iterations per correction solve */
+  double inner_ratio;   /* HS_FP32_REFINED: a correction solve stops when its force norm is
+                           below inner_ratio times the FP64 residual's */
+} hs_options;
+
+/* Fill *opt with defaults: FP64, check_every 8, double outputs,
+ * inner_max 200, inner_ratio 1e-3. */
+hs_status hs_default_options(hs_options* opt);
+
+/* Device workspace (bytes) that hs_create needs for this grid, precision and
+ * number of phases.  The caller allocates it (e.g. as a PyTorch tensor) and
+ * keeps it alive until hs_destroy. */
+hs_status hs_workspace_size(const int grid[3], int nphase, const hs_options* opt, size_t* bytes);
+
+/* Create a solver for one microstructure.
+ *  grid       N1, N2, N3: even, 4..512, factors 2 and 3 only (Section 2.1 requires even N_i).
+ *  m          microstructure; copied to the device here.
+ *  C0         host 6x6 Voigt stiffness of the homogeneous reference medium lambda0 (Section 2.3),
+ *             symmetric positive definite; NULL picks it: for two isotropic phases the rule of the
+ *             paper's contrast study (Section 3.4: same Poisson ratio, k0 = a k_m + (1-a) k_i with
+ *             a = 0.55 if k_i < k_m else 0.45), otherwise an isotropic medium whose bulk modulus and
+ *             shear eigenvalue are the midpoints of the phases' ranges.
+ *  opt        options (NULL = defaults).
+ *  workspace  device memory of at least hs_workspace_size() bytes, 256-byte aligned, owned by the
+ *             caller, in use until hs_destroy.
+ *  stream     cudaStream_t to run on (NULL = legacy default stream).
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED_SIZE, HS_ERR_OOM, HS_ERR_CUDA. */
+hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const double C0[36],
+                    const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Solve for one applied macroscopic strain (Algorithm 1 under strain control).
+ *  E          host, 6 tensor components in Voigt order; must not be all zero.
+ *  tol        stop at the first evaluation with err < tol (tol = 0: run max_iter evaluations).
+ *  max_iter   maximum number of residual evaluations (>= 1).  The iteration count is the
+ *             number of residual evaluations: a homogeneous medium converges in 1.
+ *  eps_out, sig_out  device pointers [6][N3][N2][N1] (double, or float if opt.out_f32), or NULL:
+ *             eps = E + 1/2(deps^T1 + deps^T2) (tensor components), sigma = 1/2(sigma^T1+sigma^T2).
+ *  sig_eff    host, 6: <sigma> in Voigt order (the effective stress).
+ *  iters      host: residual evaluations used.   final_err: host: err of the last evaluation.
+ * Starts from u = 0 unless hs_set_state was called since the last solve.
+ * Returns HS_OK, HS_NOT_CONVERGED (outputs written for the last iterate), HS_DIVERGED, or an
+ * error. */
+hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps_out,
+                   void* sig_out, double sig_eff[6], int* iters, double* final_err);
+
+/* Error after each residual evaluation of the last hs_solve (HS_FP32_REFINED: of each FP64
+ * residual sweep).  Writes min(n, available) values; *n_written gets the count. */
+hs_status hs_err_history(const hs_ctx* c, double* out, int n, int* n_written);
+
+/* Displacement state u(q) after the last solve, as complex128 [3][N3][N2][N1/2+1]
+ * (interleaved re, im), device pointer.  Convention: the corner at (l+1/2, m+1/2, n+1/2)
+ * carries index (l, m, n) and u(q) = 1/N sum_c u(c) exp(-i q.c), i.e. the paper's u(q) of
+ * Eq. FT_u times exp(i q.(1/2,1/2,1/2)).  Not available in HS_FP32_REFINED mode. */
+hs_status hs_get_state(hs_ctx* c, void* uhat);
+
+/* Load a displacement state (same format, device pointer) as the starting point of the next
+ * hs_solve (warm start / checkpoint resume).  Not available in HS_FP32_REFINED mode. */
+hs_status hs_set_state(hs_ctx* c, const void* uhat);
+
+/* The reference medium in use (host, 6x6 Voigt). */
+hs_status hs_get_reference_medium(const hs_ctx* c, double C0[36]);
+
+/* Kernel classes reported by hs_profile_read. */
+enum {
+  HS_K_XPASS = 0,     /* fused x-pass: inverse x FFT, stencil, constitutive step, adjoint, forward x FFT */
+  HS_K_YFWD = 1,      /* forward y FFT */
+  HS_K_ZGREEN = 2,    /* forward z FFT, Green update, inverse z FFT */
+  HS_K_YINV = 3,      /* inverse y FFT */
+  HS_K_RESID64 = 4,   /* FP64 real-space residual sweep (HS_FP32_REFINED) */
+  HS_K_FIELDS = 5,    /* output of eps and sigma */
+  HS_K_OTHER = 6,     /* state transforms, correction accumulation, set-up */
+  HS_K_COUNT = 7
+};
+
+/* Start (on != 0) or stop per-launch timing: every kernel launch of this context is then
+ * bracketed by CUDA events on the context's stream and counted by class.  Timing adds a few
+ * microseconds of host work per launch and no device work. */
+hs_status hs_profile_enable(hs_ctx* c, int on);
+
+/* Accumulated device time (ms, from the events) and launch counts per kernel class since the
+ * last read or enable; resets the accumulators.  ms and launches have HS_K_COUNT entries.
+ * Launch counts are kept whether or not timing is enabled. */
+hs_status hs_profile_read(hs_ctx* c, double ms[7], long long launches[7]);
+
+/* Release the context (the workspace stays the caller's). */
+void hs_destroy(hs_ctx* c);
+
+/* Static description of a status code. */
+const char* hs_error_string(hs_status s);
+
+/* Text of the last error recorded on this context ("" if none). */
+const char* hs_last_error(const hs_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_H */

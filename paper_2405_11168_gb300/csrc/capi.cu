@@ -1,0 +1,1010 @@
+// Host side of the C ABI declared in include/hs.h.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <cmath>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/hs.h"
+#include "launch.h"
+
+using hs::DevStatus;
+using hs::FftPlan;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kHistCap = 1 << 16;
+constexpr int kMaxN = 512;
+constexpr int kTargetBlocks = 608;  // 4 x 152 SMs
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool make_plan(int L, FftPlan* p) {
+  p->L = L;
+  p->nstage = 0;
+  p->packed = 0;
+  int r = L;
+  auto push = [&](int R) {
+    if (p->nstage >= hs::kMaxStages) return false;
+    p->packed |= R << (4 * p->nstage);
+    p->nstage++;
+    r /= R;
+    return true;
+  };
+  while (r % 8 == 0)
+    if (!push(8)) return false;
+  while (r % 4 == 0)
+    if (!push(4)) return false;
+  while (r % 2 == 0)
+    if (!push(2)) return false;
+  while (r % 3 == 0)
+    if (!push(3)) return false;
+  return r == 1 && p->nstage > 0;
+}
+
+// w_L^j = exp(-2 pi i j / L), j < L, with exact values on the quarter points
+void twiddles(int L, std::vector<double>& re, std::vector<double>& im) {
+  re.resize(L);
+  im.resize(L);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int j = 0; j < L; ++j) {
+    if ((4 * j) % L == 0) {
+      const int q = (4 * j) / L;  // quarter turns
+      static const double cr[4] = {1, 0, -1, 0}, ci[4] = {0, -1, 0, 1};
+      re[j] = cr[q];
+      im[j] = ci[q];
+      continue;
+    }
+    const long double t = 2.0L * pi * (long double)j / (long double)L;
+    re[j] = (double)cosl(t);
+    im[j] = (double)-sinl(t);
+  }
+}
+
+// Voigt index of tensor pair (i, j), order 11,22,33,23,13,12
+int vidx(int i, int j) {
+  static const int V[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+  return V[i][j];
+}
+
+bool is_isotropic(const double* C, double* lam, double* mu) {
+  double scale = 0;
+  for (int i = 0; i < 36; ++i) scale = std::max(scale, fabs(C[i]));
+  const double tol = 1e-12 * std::max(scale, 1e-300);
+  const double l = C[1], m = C[21];  // C[0][1], C[3][3]
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double want = 0;
+      if (i < 3 && j < 3) want = (i == j) ? l + 2 * m : l;
+      else if (i == j) want = m;
+      if (fabs(C[i * 6 + j] - want) > tol) return false;
+    }
+  *lam = l;
+  *mu = m;
+  return true;
+}
+
+// eigenvalues of a symmetric n x n matrix (cyclic Jacobi), n <= 6
+void sym_eig(std::vector<double> a, int n, std::vector<double>& ev) {
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[p * n + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (a[q * n + q] - a[p * n + p]) / (2 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1));
+        const double c = 1 / sqrt(t * t + 1), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = c * akp - s * akq;
+          a[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = c * apk - s * aqk;
+          a[q * n + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  ev.resize(n);
+  for (int i = 0; i < n; ++i) ev[i] = a[i * n + i];
+}
+
+// Voigt bulk modulus and the range of deviatoric eigenvalues (Mandel form)
+void bulk_and_shear_range(const double* C, double* K, double* dmin, double* dmax) {
+  double s = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) s += C[i * 6 + j];
+  *K = s / 9.0;
+  const double r2 = sqrt(2.0);
+  double M[36];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) M[i * 6 + j] = C[i * 6 + j] * (i < 3 ? 1 : r2) * (j < 3 ? 1 : r2);
+  // orthonormal basis of the deviatoric subspace
+  double B[5][6] = {{1 / r2, -1 / r2, 0, 0, 0, 0},
+                    {1 / sqrt(6.0), 1 / sqrt(6.0), -2 / sqrt(6.0), 0, 0, 0},
+                    {0, 0, 0, 1, 0, 0},
+                    {0, 0, 0, 0, 1, 0},
+                    {0, 0, 0, 0, 0, 1}};
+  std::vector<double> D(25, 0.0);
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) {
+      double v = 0;
+      for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) v += B[a][i] * M[i * 6 + j] * B[b][j];
+      D[a * 5 + b] = v;
+    }
+  std::vector<double> ev;
+  sym_eig(D, 5, ev);
+  *dmin = *std::min_element(ev.begin(), ev.end());
+  *dmax = *std::max_element(ev.begin(), ev.end());
+}
+
+void iso_voigt(double lam, double mu, double* C) {
+  for (int i = 0; i < 36; ++i) C[i] = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[i * 6 + j] = (i == j) ? lam + 2 * mu : lam;
+  for (int i = 3; i < 6; ++i) C[i * 6 + i] = mu;
+}
+
+bool cholesky_pd(const double* A) {
+  double L[36] = {0};
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[i * 6 + j];
+      for (int k = 0; k < j; ++k) s -= L[i * 6 + k] * L[j * 6 + k];
+      if (i == j) {
+        if (!(s > 0)) return false;
+        L[i * 6 + i] = sqrt(s);
+      } else {
+        L[i * 6 + j] = s / L[j * 6 + j];
+      }
+    }
+  return true;
+}
+
+struct Layout {
+  size_t S, B0, B1, ids, matk, matd, tw, partials, status, hist, u64, rsrc, total;
+};
+
+}  // namespace
+
+struct hs_ctx {
+  int n1, n2, n3, nh, P;
+  size_t N;
+  int prec;
+  bool f64;  // iteration kernels in FP64
+  hs_options opt;
+  cudaStream_t stream;
+  int nphase;
+  bool iso;
+  std::vector<double> table;
+  double C0[36];
+  double G6[36];
+  char* ws;
+  size_t ws_bytes;
+  Layout lay;
+  void* S;
+  void* B[2];
+  uint16_t* ids;
+  void* matk;
+  double* matd;
+  void* twk[3];
+  double* partials;
+  DevStatus* st;
+  double* hist;
+  double* u64;
+  float* rsrc;
+  FftPlan plan[3];
+  int ty, zc, nthr_m;
+  dim3 grid_m;
+  int ct, nthr_y, nthr_z;
+  size_t smem_y, smem_z;
+  dim3 grid_y, grid_z;
+  bool warm;
+  int cur;
+  std::vector<double> hist_host;
+  std::string last_err;
+  // profiling
+  bool prof;
+  long long launches[HS_K_COUNT];
+  struct Ev { int kind; cudaEvent_t a, b; };
+  std::vector<Ev> ev_used;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace {
+
+hs_status fail(hs_ctx* c, hs_status s, const std::string& msg) {
+  g_last_error = msg;
+  if (c) c->last_err = msg;
+  return s;
+}
+
+hs_status cuda_fail(hs_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, HS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Bracket one kernel launch: count it and, when profiling, record events.
+struct LaunchScope {
+  hs_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(hs_ctx* c_, int kind_) : c(c_), kind(kind_) {
+    c->launches[kind]++;
+    if (c->prof) {
+      a = take();
+      b = take();
+      if (a) cudaEventRecord(a, c->stream);
+    }
+  }
+  cudaEvent_t take() {
+    cudaEvent_t e = nullptr;
+    if (!c->ev_pool.empty()) {
+      e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+    }
+    return e;
+  }
+  ~LaunchScope() {
+    if (a && b) {
+      cudaEventRecord(b, c->stream);
+      c->ev_used.push_back({kind, a, b});
+    } else {
+      if (a) c->ev_pool.push_back(a);
+      if (b) c->ev_pool.push_back(b);
+    }
+  }
+};
+
+#define HS_CU(c, call)                                    \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, #call); \
+  } while (0)
+
+hs_status check_grid(const int grid[3]) {
+  for (int i = 0; i < 3; ++i) {
+    const int n = grid[i];
+    if (n < 4 || n > kMaxN || (n % 2) != 0) return HS_ERR_UNSUPPORTED_SIZE;
+    FftPlan p;
+    if (!make_plan(n, &p)) return HS_ERR_UNSUPPORTED_SIZE;
+  }
+  return HS_OK;
+}
+
+int pitch_of(int nh, bool f64) { return f64 ? ((nh + 1) & ~1) : ((nh + 3) & ~3); }
+
+int pick_ty(int n2) { return (n2 % 4 == 0) ? 4 : 2; }
+
+size_t march_smem(int n1, int ty, bool f64, int mode, bool real) {
+  const size_t cs = f64 ? 16 : 8, rs = f64 ? 8 : 4;
+  const int NR = ty + 2, NSI = 3 * NR / 2, NSF = 3 * ty / 2;
+  const int nthr = ((n1 + 31) / 32) * 32, nw = nthr / 32;
+  size_t ring = real ? 8 * 2 * 3 * NR * (size_t)n1 : cs * 2 * NSI * (size_t)n1;
+  size_t fbuf = (real || mode != hs::MODE_FORCE) ? 0 : cs * NSF * (size_t)n1;
+  size_t edge = ((real ? 8 : rs) * nw * (ty + 1) * 12 + 15) & ~size_t(15);
+  size_t red = 32 * hs::NRED * 8;
+  return ring + fbuf + edge + red;
+}
+
+Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
+  Layout L;
+  const bool f64 = (prec == HS_FP64);
+  const int nh = n1 / 2 + 1, P = pitch_of(nh, f64);
+  const size_t cs = f64 ? 16 : 8;
+  const size_t N = (size_t)n1 * n2 * n3;
+  const size_t cbuf = align256((size_t)3 * n3 * n2 * P * cs);
+  const int ty = pick_ty(n2);
+  const size_t max_blocks = (size_t)(n2 / ty) * n3;  // upper bound over z-chunkings
+  size_t off = 0;
+  L.S = off; off += cbuf;
+  L.B0 = off; off += cbuf;
+  L.B1 = off; off += cbuf;
+  L.ids = off; off += align256(N * 2);
+  L.matk = off; off += align256((size_t)nphase * 21 * (f64 ? 8 : 4));
+  L.matd = off; off += align256((size_t)nphase * 21 * 8);
+  L.tw = off; off += align256((size_t)(n1 + n2 + n3) * cs);
+  L.partials = off; off += align256(max_blocks * hs::NRED * 8);
+  L.status = off; off += align256(sizeof(DevStatus));
+  L.hist = off; off += align256((size_t)kHistCap * 8);
+  L.u64 = off;
+  L.rsrc = off;
+  if (prec == HS_FP32_REFINED) {
+    L.u64 = off; off += align256(3 * N * 8);
+    L.rsrc = off; off += align256(3 * N * 4);
+  }
+  L.total = off;
+  return L;
+}
+
+template <typename T> void fill_march_common(hs_ctx* c, hs::MarchArgs<T>& a) {
+  memset(&a, 0, sizeof(a));
+  a.ids = c->ids;
+  a.mat = (const T*)(sizeof(T) == 8 && !c->f64 ? (void*)c->matd : c->matk);
+  a.tw1 = (const typename hs::cplx_t<T>::type*)c->twk[0];
+  a.plan1 = c->plan[0];
+  a.n1 = c->n1;
+  a.n2 = c->n2;
+  a.n3 = c->n3;
+  a.P = c->P;
+  a.zc = c->zc;
+  a.partials = c->partials;
+  a.st = c->st;
+  a.hist = c->hist;
+}
+
+template <typename T> void fill_col(hs_ctx* c, hs::ColArgs<T>& a, void* buf, int axis) {
+  using C = typename hs::cplx_t<T>::type;
+  memset(&a, 0, sizeof(a));
+  a.buf = (C*)buf;
+  a.S = (C*)c->S;
+  a.tw = (const C*)c->twk[axis];
+  a.tw1 = (const C*)c->twk[0];
+  a.tw2 = (const C*)c->twk[1];
+  a.tw3 = (const C*)c->twk[2];
+  a.plan = c->plan[axis];
+  a.n1 = c->n1;
+  a.n2 = c->n2;
+  a.n3 = c->n3;
+  a.P = c->P;
+  a.nh = c->nh;
+  a.scale = (T)(2.0 / (double)c->N);
+  for (int i = 0; i < 36; ++i) a.G6[i] = (T)c->G6[i];
+  a.st = c->st;
+  a.skip_if_done = 1;
+}
+
+template <typename T> hs_status launch_force(hs_ctx* c, const double E[6], int in, const float* src) {
+  hs::MarchArgs<T> a;
+  fill_march_common<T>(c, a);
+  a.in = (const typename hs::cplx_t<T>::type*)c->B[in];
+  a.out = (typename hs::cplx_t<T>::type*)c->B[in ^ 1];
+  for (int i = 0; i < 6; ++i) a.E[i] = (T)E[i];
+  a.src = src;
+  a.skip_if_done = 1;
+  const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, hs::MODE_FORCE, false);
+  LaunchScope ls(c, HS_K_XPASS);
+  cudaError_t e = hs::launch_march<T>(a, c->iso, c->ty, hs::MODE_FORCE, false, c->grid_m, c->nthr_m, sm, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_march(force)");
+  return HS_OK;
+}
+
+template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
+  hs::ColArgs<T> a;
+  cudaError_t e;
+  fill_col<T>(c, a, c->B[buf], 1);
+  {
+    LaunchScope ls(c, HS_K_YFWD);
+    e = hs::launch_col<T>(a, hs::COL_Y_FWD, c->ct, c->grid_y, c->nthr_y, c->smem_y, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y fwd)");
+  fill_col<T>(c, a, c->B[buf], 2);
+  {
+    LaunchScope ls(c, HS_K_ZGREEN);
+    e = hs::launch_col<T>(a, hs::COL_Z_GREEN, c->ct, c->grid_z, c->nthr_z, c->smem_z, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z green)");
+  fill_col<T>(c, a, c->B[buf], 1);
+  {
+    LaunchScope ls(c, HS_K_YINV);
+    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, c->grid_y, c->nthr_y, c->smem_y, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y inv)");
+  return HS_OK;
+}
+
+// state S -> buffer (inverse z then inverse y): the x-pass input of u = S
+template <typename T> hs_status launch_state_to_buf(hs_ctx* c, int buf) {
+  hs::ColArgs<T> a;
+  fill_col<T>(c, a, c->B[buf], 2);
+  a.skip_if_done = 0;
+  cudaError_t e;
+  {
+    LaunchScope ls(c, HS_K_OTHER);
+    e = hs::launch_col<T>(a, hs::COL_Z_INV_STATE, c->ct, c->grid_z, c->nthr_z, c->smem_z, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z inv state)");
+  fill_col<T>(c, a, c->B[buf], 1);
+  a.skip_if_done = 0;
+  {
+    LaunchScope ls(c, HS_K_OTHER);
+    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, c->grid_y, c->nthr_y, c->smem_y, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y inv)");
+  return HS_OK;
+}
+
+template <typename T> hs_status launch_fields(hs_ctx* c, const double E[6], int in, void* eps, void* sig) {
+  hs::MarchArgs<T> a;
+  fill_march_common<T>(c, a);
+  a.in = (const typename hs::cplx_t<T>::type*)c->B[in];
+  for (int i = 0; i < 6; ++i) a.E[i] = (T)E[i];
+  a.eps_out = eps;
+  a.sig_out = sig;
+  a.out_f32 = c->opt.out_f32;
+  a.skip_if_done = 0;
+  const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, hs::MODE_FIELDS, false);
+  LaunchScope ls(c, HS_K_FIELDS);
+  cudaError_t e = hs::launch_march<T>(a, c->iso, c->ty, hs::MODE_FIELDS, false, c->grid_m, c->nthr_m, sm, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_march(fields)");
+  return HS_OK;
+}
+
+hs_status reset_status(hs_ctx* c, double tol, int max_iter, double denom) {
+  DevStatus h;
+  memset(&h, 0, sizeof(h));
+  h.max_iter = max_iter;
+  h.hist_cap = kHistCap;
+  h.tol = tol;
+  h.denom = denom;
+  h.nvox = (double)c->N;
+  HS_CU(c, cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  return HS_OK;
+}
+
+hs_status read_status(hs_ctx* c, DevStatus* h) {
+  HS_CU(c, cudaMemcpyAsync(h, c->st, sizeof(*h), cudaMemcpyDeviceToHost, c->stream));
+  HS_CU(c, cudaStreamSynchronize(c->stream));
+  return HS_OK;
+}
+
+size_t cbuf_bytes(const hs_ctx* c) {
+  return (size_t)3 * c->n3 * c->n2 * c->P * (c->f64 ? 16 : 8);
+}
+
+// Basic-scheme iterations until the device status says done.  Buffer c->cur
+// holds the x-pass input on entry.  Returns the index of the buffer that
+// holds the x-pass input of the last evaluation.
+template <typename T>
+hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst, int* last_in) {
+  const int cur0 = c->cur;
+  int cur = cur0;
+  const int chunk = std::max(1, c->opt.check_every);
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      hs_status s = launch_force<T>(c, E, cur, src);
+      if (s != HS_OK) return s;
+      s = launch_cols<T>(c, cur ^ 1);
+      if (s != HS_OK) return s;
+      cur ^= 1;
+    }
+    hs_status s = read_status(c, hst);
+    if (s != HS_OK) return s;
+    if (hst->done) break;
+  }
+  *last_in = cur0 ^ ((hst->evals - 1) & 1);
+  return HS_OK;
+}
+
+hs_status status_code(const DevStatus& h) {
+  if (h.done == hs::DONE_CONVERGED) return HS_OK;
+  if (h.done == hs::DONE_DIVERGED) return HS_DIVERGED;
+  return HS_NOT_CONVERGED;
+}
+
+template <typename T>
+hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps, void* sig,
+                      double sig_eff[6], int* iters, double* final_err) {
+  hs_status s = reset_status(c, tol, max_iter, 0.0);
+  if (s != HS_OK) return s;
+  c->cur = 0;
+  if (c->warm) {
+    s = launch_state_to_buf<T>(c, 0);
+    if (s != HS_OK) return s;
+    c->warm = false;
+  } else {
+    HS_CU(c, cudaMemsetAsync(c->S, 0, cbuf_bytes(c), c->stream));
+    HS_CU(c, cudaMemsetAsync(c->B[0], 0, cbuf_bytes(c), c->stream));
+  }
+  DevStatus h;
+  int last_in = 0;
+  s = iterate<T>(c, E, nullptr, &h, &last_in);
+  if (s != HS_OK) return s;
+  if (eps != nullptr && sig != nullptr) {
+    s = launch_fields<T>(c, E, last_in, eps, sig);
+    if (s != HS_OK) return s;
+  }
+  HS_CU(c, cudaStreamSynchronize(c->stream));
+  const int n = std::min(h.evals, kHistCap);
+  c->hist_host.resize(n);
+  if (n) HS_CU(c, cudaMemcpy(c->hist_host.data(), c->hist, n * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 6; ++i) sig_eff[i] = h.sig_mean[i];
+  if (iters) *iters = h.evals;
+  if (final_err) *final_err = h.err;
+  return status_code(h);
+}
+
+// FP64 real-space residual sweep on u64: force -> rsrc (float), status -> err
+hs_status launch_residual64(hs_ctx* c, const double E[6], int mode, void* eps, void* sig) {
+  hs::MarchArgs<double> a;
+  fill_march_common<double>(c, a);
+  a.mat = c->matd;
+  for (int i = 0; i < 6; ++i) a.E[i] = E[i];
+  a.u64 = c->u64;
+  a.fout = c->rsrc;
+  a.eps_out = eps;
+  a.sig_out = sig;
+  a.out_f32 = c->opt.out_f32;
+  a.skip_if_done = 0;
+  const size_t sm = march_smem(c->n1, c->ty, true, mode, true);
+  LaunchScope ls(c, mode == hs::MODE_FORCE ? HS_K_RESID64 : HS_K_FIELDS);
+  cudaError_t e = hs::launch_march<double>(a, c->iso, c->ty, mode, true, c->grid_m, c->nthr_m, sm, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_march(residual fp64)");
+  return HS_OK;
+}
+
+hs_status launch_emit(hs_ctx* c, int in) {
+  hs::MarchArgs<float> a;
+  fill_march_common<float>(c, a);
+  a.in = (const float2*)c->B[in];
+  a.u64 = c->u64;
+  a.skip_if_done = 0;
+  const size_t sm = march_smem(c->n1, c->ty, false, hs::MODE_EMIT, false);
+  LaunchScope ls(c, HS_K_OTHER);
+  cudaError_t e = hs::launch_march<float>(a, true, c->ty, hs::MODE_EMIT, false, c->grid_m, c->nthr_m, sm, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_march(emit)");
+  return HS_OK;
+}
+
+hs_status solve_refined(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps, void* sig,
+                        double sig_eff[6], int* iters, double* final_err) {
+  HS_CU(c, cudaMemsetAsync(c->u64, 0, 3 * c->N * sizeof(double), c->stream));
+  c->hist_host.clear();
+  int total = 0;
+  DevStatus h64, hin;
+  const double zeroE[6] = {0, 0, 0, 0, 0, 0};
+  hs_status result = HS_NOT_CONVERGED;
+  for (;;) {
+    hs_status s = reset_status(c, 0.0, 1 << 30, 0.0);
+    if (s != HS_OK) return s;
+    s = launch_residual64(c, E, hs::MODE_FORCE, nullptr, nullptr);
+    if (s != HS_OK) return s;
+    s = read_status(c, &h64);
+    if (s != HS_OK) return s;
+    total += 1;
+    c->hist_host.push_back(h64.err);
+    if (!(h64.err == h64.err) || h64.err > 1e300) { result = HS_DIVERGED; break; }
+    if (h64.err < tol) { result = HS_OK; break; }
+    if (total >= max_iter) { result = HS_NOT_CONVERGED; break; }
+    // correction solve: K du = -r in FP32, source r = rsrc, macro strain 0
+    const int budget = std::min(std::max(1, c->opt.inner_max), max_iter - total);
+    s = reset_status(c, c->opt.inner_ratio * h64.err, budget, h64.sig_norm);
+    if (s != HS_OK) return s;
+    HS_CU(c, cudaMemsetAsync(c->S, 0, cbuf_bytes(c), c->stream));
+    HS_CU(c, cudaMemsetAsync(c->B[0], 0, cbuf_bytes(c), c->stream));
+    c->cur = 0;
+    int last_in = 0;
+    s = iterate<float>(c, zeroE, c->rsrc, &hin, &last_in);
+    if (s != HS_OK) return s;
+    total += hin.evals;
+    if (hin.done == hs::DONE_DIVERGED) { result = HS_DIVERGED; break; }
+    // u64 += du, du = inverse transform of the correction state
+    s = launch_state_to_buf<float>(c, 0);
+    if (s != HS_OK) return s;
+    s = launch_emit(c, 0);
+    if (s != HS_OK) return s;
+  }
+  if (eps != nullptr && sig != nullptr) {
+    hs_status s = launch_residual64(c, E, hs::MODE_FIELDS, eps, sig);
+    if (s != HS_OK) return s;
+  }
+  HS_CU(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 6; ++i) sig_eff[i] = h64.sig_mean[i];
+  if (iters) *iters = total;
+  if (final_err) *final_err = h64.err;
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_status hs_default_options(hs_options* opt) {
+  if (!opt) return HS_ERR_INVALID_ARG;
+  opt->precision = HS_FP64;
+  opt->check_every = 8;
+  opt->out_f32 = 0;
+  opt->inner_max = 200;
+  opt->inner_ratio = 1e-3;
+  return HS_OK;
+}
+
+hs_status hs_workspace_size(const int grid[3], int nphase, const hs_options* opt, size_t* bytes) {
+  if (!grid || !bytes || nphase < 1 || nphase > 65536) return fail(nullptr, HS_ERR_INVALID_ARG, "bad argument");
+  hs_options o;
+  hs_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED) return fail(nullptr, HS_ERR_INVALID_ARG, "bad precision");
+  hs_status s = check_grid(grid);
+  if (s != HS_OK) return fail(nullptr, s, "unsupported grid size");
+  *bytes = make_layout(grid[0], grid[1], grid[2], nphase, o.precision).total;
+  return HS_OK;
+}
+
+hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const double C0[36],
+                    const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out || !grid || !m || !m->ids || !m->table || !workspace)
+    return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  hs_options o;
+  hs_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED || o.check_every < 1 || o.inner_max < 1 ||
+      !(o.inner_ratio > 0 && o.inner_ratio < 1))
+    return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
+  if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
+  if (m->nphase < 1 || m->nphase > 65536)
+    return fail(nullptr, HS_ERR_INVALID_ARG, "bad nphase");
+  hs_status s = check_grid(grid);
+  if (s != HS_OK) return fail(nullptr, s, "unsupported grid size (even, 4..512, factors 2 and 3)");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(nullptr, HS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  // material table checks
+  const int np = m->nphase;
+  std::vector<double> table(m->table, m->table + (size_t)np * 36);
+  bool all_iso = true;
+  std::vector<double> lam(np), mu(np);
+  for (int p = 0; p < np; ++p) {
+    const double* C = &table[(size_t)p * 36];
+    double scale = 0;
+    for (int i = 0; i < 36; ++i) {
+      if (!std::isfinite(C[i])) return fail(nullptr, HS_ERR_INVALID_ARG, "non-finite stiffness");
+      scale = std::max(scale, fabs(C[i]));
+    }
+    for (int i = 0; i < 6; ++i) {
+      if (C[i * 6 + i] < 0) return fail(nullptr, HS_ERR_INVALID_ARG, "negative stiffness diagonal");
+      for (int j = 0; j < i; ++j)
+        if (fabs(C[i * 6 + j] - C[j * 6 + i]) > 1e-12 * scale)
+          return fail(nullptr, HS_ERR_INVALID_ARG, "stiffness table not symmetric");
+    }
+    if (!is_isotropic(C, &lam[p], &mu[p])) all_iso = false;
+  }
+  // reference medium
+  double C0v[36];
+  if (C0) {
+    for (int i = 0; i < 36; ++i) C0v[i] = C0[i];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < i; ++j)
+        if (fabs(C0v[i * 6 + j] - C0v[j * 6 + i]) > 1e-12 * fabs(C0v[0]))
+          return fail(nullptr, HS_ERR_INVALID_ARG, "C0 not symmetric");
+    if (!cholesky_pd(C0v)) return fail(nullptr, HS_ERR_INVALID_ARG, "C0 not positive definite");
+  } else if (np == 2 && all_iso) {
+    // Section 3.4: same Poisson ratio, k0 = alpha k_m + (1 - alpha) k_i
+    const double km = lam[0] + 2 * mu[0] / 3, ki = lam[1] + 2 * mu[1] / 3;
+    const double alpha = (ki < km) ? 0.55 : 0.45;
+    const double k0 = alpha * km + (1 - alpha) * ki;
+    const double nu0 = lam[0] / (2 * (lam[0] + mu[0]));
+    const double mu0 = 3 * k0 * (1 - 2 * nu0) / (2 * (1 + nu0));
+    iso_voigt(k0 - 2 * mu0 / 3, mu0, C0v);
+    if (!cholesky_pd(C0v)) return fail(nullptr, HS_ERR_INVALID_ARG, "reference medium not positive definite");
+  } else {
+    double kmin = 1e300, kmax = -1e300, dmin = 1e300, dmax = -1e300;
+    for (int p = 0; p < np; ++p) {
+      double K, d0, d1;
+      bulk_and_shear_range(&table[(size_t)p * 36], &K, &d0, &d1);
+      kmin = std::min(kmin, K);
+      kmax = std::max(kmax, K);
+      dmin = std::min(dmin, d0);
+      dmax = std::max(dmax, d1);
+    }
+    const double k0 = 0.5 * (kmin + kmax), mu0 = 0.25 * (dmin + dmax);
+    iso_voigt(k0 - 2 * mu0 / 3, mu0, C0v);
+    if (!cholesky_pd(C0v)) return fail(nullptr, HS_ERR_INVALID_ARG, "reference medium not positive definite");
+  }
+
+  hs_ctx* c = new hs_ctx();
+  c->n1 = grid[0];
+  c->n2 = grid[1];
+  c->n3 = grid[2];
+  c->nh = c->n1 / 2 + 1;
+  c->prec = o.precision;
+  c->f64 = (o.precision == HS_FP64);
+  c->P = pitch_of(c->nh, c->f64);
+  c->N = (size_t)c->n1 * c->n2 * c->n3;
+  c->opt = o;
+  c->stream = (cudaStream_t)stream;
+  c->nphase = np;
+  c->iso = all_iso;
+  c->table = table;
+  memcpy(c->C0, C0v, sizeof(C0v));
+  // Omega^-1_jl = sum_ik lambda0_jikl M_ik, M symmetric: G6[(j,l)][(i,k)]
+  static const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) {
+      const int j = pr[a][0], l = pr[a][1], i = pr[b][0], k = pr[b][1];
+      double g = C0v[vidx(j, i) * 6 + vidx(k, l)];
+      if (i != k) g += C0v[vidx(j, k) * 6 + vidx(i, l)];
+      c->G6[a * 6 + b] = g;
+    }
+  c->lay = make_layout(c->n1, c->n2, c->n3, np, o.precision);
+  if (workspace_bytes < c->lay.total) {
+    delete c;
+    return fail(nullptr, HS_ERR_OOM, "workspace too small");
+  }
+  c->ws = (char*)workspace;
+  c->ws_bytes = workspace_bytes;
+  c->S = c->ws + c->lay.S;
+  c->B[0] = c->ws + c->lay.B0;
+  c->B[1] = c->ws + c->lay.B1;
+  c->ids = (uint16_t*)(c->ws + c->lay.ids);
+  c->matk = c->ws + c->lay.matk;
+  c->matd = (double*)(c->ws + c->lay.matd);
+  c->partials = (double*)(c->ws + c->lay.partials);
+  c->st = (DevStatus*)(c->ws + c->lay.status);
+  c->hist = (double*)(c->ws + c->lay.hist);
+  c->u64 = (o.precision == HS_FP32_REFINED) ? (double*)(c->ws + c->lay.u64) : nullptr;
+  c->rsrc = (o.precision == HS_FP32_REFINED) ? (float*)(c->ws + c->lay.rsrc) : nullptr;
+  c->warm = false;
+  c->cur = 0;
+  c->prof = false;
+  for (int k = 0; k < HS_K_COUNT; ++k) c->launches[k] = 0;
+  for (int ax = 0; ax < 3; ++ax) make_plan(grid[ax], &c->plan[ax]);
+
+  // launch configuration
+  c->ty = pick_ty(c->n2);
+  c->nthr_m = ((c->n1 + 31) / 32) * 32;
+  const int ytiles = c->n2 / c->ty;
+  int nzc = std::max(1, std::min(c->n3, (kTargetBlocks + ytiles - 1) / ytiles));
+  c->zc = (c->n3 + nzc - 1) / nzc;
+  nzc = (c->n3 + c->zc - 1) / c->zc;
+  c->grid_m = dim3(ytiles, nzc);
+  c->ct = c->f64 ? 8 : 16;
+  const int maxthr = c->f64 ? 384 : 768;
+  auto col_threads = [&](int L) {
+    const int T = (L + hs::kE - 1) / hs::kE;
+    int n = 3 * c->ct * T;
+    n = ((n + 31) / 32) * 32;
+    return std::min(n, (maxthr / T) * T);
+  };
+  c->nthr_y = col_threads(c->n2);
+  c->nthr_z = col_threads(c->n3);
+  const size_t cs = c->f64 ? 16 : 8;
+  c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
+  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs;
+  const int xtiles = (c->nh + c->ct - 1) / c->ct;
+  c->grid_y = dim3(xtiles, c->n3);
+  c->grid_z = dim3(xtiles, c->n2);
+  // shared memory limits
+  int dev = 0, smem_optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    hs_status st = cuda_fail(nullptr, e, "device query");
+    delete c;
+    return st;
+  }
+  const size_t need = std::max({march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, false),
+                                o.precision == HS_FP32_REFINED ? march_smem(c->n1, c->ty, true, hs::MODE_FORCE, true) : 0,
+                                c->smem_y, c->smem_z});
+  if (need > (size_t)smem_optin) {
+    delete c;
+    return fail(nullptr, HS_ERR_UNSUPPORTED_SIZE, "grid too large for shared-memory tiles");
+  }
+
+  // twiddles / phase tables in kernel precision
+  {
+    std::vector<double> tw;
+    for (int ax = 0; ax < 3; ++ax) {
+      std::vector<double> re, im;
+      twiddles(grid[ax], re, im);
+      for (int j = 0; j < grid[ax]; ++j) {
+        tw.push_back(re[j]);
+        tw.push_back(im[j]);
+      }
+    }
+    char* twp = c->ws + c->lay.tw;
+    size_t off = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      c->twk[ax] = twp + off;
+      off += (size_t)grid[ax] * cs;
+    }
+    if (c->f64) {
+      e = cudaMemcpyAsync(twp, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    } else {
+      std::vector<float> twf(tw.begin(), tw.end());
+      e = cudaMemcpyAsync(twp, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      hs_status st = cuda_fail(nullptr, e, "twiddle upload");
+      delete c;
+      return st;
+    }
+    std::vector<double> md((size_t)np * 21);
+    for (int p = 0; p < np; ++p) {
+      const double* C = &table[(size_t)p * 36];
+      if (all_iso) {
+        md[(size_t)p * 2] = lam[p];
+        md[(size_t)p * 2 + 1] = mu[p];
+      } else {
+        int k = 0;
+        for (int i = 0; i < 6; ++i)
+          for (int j = i; j < 6; ++j) md[(size_t)p * 21 + k++] = C[i * 6 + j];
+      }
+    }
+    e = cudaMemcpyAsync(c->matd, md.data(), md.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+      if (c->f64) {
+        e = cudaMemcpyAsync(c->matk, md.data(), md.size() * 8, cudaMemcpyHostToDevice, c->stream);
+      } else {
+        std::vector<float> mf(md.begin(), md.end());
+        e = cudaMemcpyAsync(c->matk, mf.data(), mf.size() * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      hs_status st = cuda_fail(nullptr, e, "material upload");
+      delete c;
+      return st;
+    }
+  }
+  // phase ids (host or device pointer), converted to uint16 on the device
+  {
+    cudaPointerAttributes attr;
+    e = cudaPointerGetAttributes(&attr, m->ids);
+    bool dev_ptr = (e == cudaSuccess) && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    if (e != cudaSuccess) cudaGetLastError();
+    const cudaMemcpyKind kind = dev_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (m->kind == HS_IDS_U16) {
+      e = cudaMemcpyAsync(c->ids, m->ids, c->N * 2, kind, c->stream);
+    } else {
+      e = cudaMemcpyAsync(c->B[0], m->ids, c->N, kind, c->stream);
+      if (e == cudaSuccess) {
+        LaunchScope ls(c, HS_K_OTHER);
+        e = hs::launch_ids_u8_to_u16((const uint8_t*)c->B[0], c->ids, c->N, c->stream);
+      }
+    }
+    int* maxid = (int*)c->partials;
+    if (e == cudaSuccess) e = cudaMemsetAsync(maxid, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) {
+      LaunchScope ls(c, HS_K_OTHER);
+      e = hs::launch_max_id(c->ids, c->N, maxid, c->stream);
+    }
+    int hmax = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hmax, maxid, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      hs_status st = cuda_fail(nullptr, e, "phase-id upload");
+      delete c;
+      return st;
+    }
+    if (hmax >= np) {
+      delete c;
+      return fail(nullptr, HS_ERR_INVALID_ARG, "phase id >= nphase");
+    }
+  }
+  *out = c;
+  return HS_OK;
+}
+
+hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps_out, void* sig_out,
+                   double sig_eff[6], int* iters, double* final_err) {
+  if (!c || !E || !sig_eff) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (!(tol >= 0) || max_iter < 1) return fail(c, HS_ERR_INVALID_ARG, "bad tol or max_iter");
+  double en = 0;
+  for (int i = 0; i < 6; ++i) {
+    if (!std::isfinite(E[i])) return fail(c, HS_ERR_INVALID_ARG, "non-finite E");
+    en += E[i] * E[i];
+  }
+  if (en == 0) return fail(c, HS_ERR_INVALID_ARG, "E = 0 (the error norm would divide by <sigma> = 0)");
+  if ((eps_out == nullptr) != (sig_out == nullptr)) return fail(c, HS_ERR_INVALID_ARG, "give both or neither field output");
+  if (eps_out) {
+    cudaPointerAttributes a1, a2;
+    cudaError_t e1 = cudaPointerGetAttributes(&a1, eps_out), e2 = cudaPointerGetAttributes(&a2, sig_out);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) cudaGetLastError();
+    if (e1 != cudaSuccess || e2 != cudaSuccess || (a1.type != cudaMemoryTypeDevice && a1.type != cudaMemoryTypeManaged) ||
+        (a2.type != cudaMemoryTypeDevice && a2.type != cudaMemoryTypeManaged))
+      return fail(c, HS_ERR_INVALID_ARG, "field outputs must be device pointers");
+  }
+  c->last_err.clear();
+  if (c->prec == HS_FP32_REFINED) return solve_refined(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err);
+  if (c->f64) return solve_plain<double>(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err);
+  return solve_plain<float>(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err);
+}
+
+hs_status hs_err_history(const hs_ctx* c, double* out, int n, int* n_written) {
+  if (!c || (!out && n > 0) || n < 0) return HS_ERR_INVALID_ARG;
+  const int k = std::min(n, (int)c->hist_host.size());
+  for (int i = 0; i < k; ++i) out[i] = c->hist_host[i];
+  if (n_written) *n_written = k;
+  return HS_OK;
+}
+
+hs_status hs_get_state(hs_ctx* c, void* uhat) {
+  if (!c || !uhat) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (c->prec == HS_FP32_REFINED) return fail(c, HS_ERR_INVALID_ARG, "state export is not available in refined mode");
+  cudaError_t e = c->f64 ? hs::launch_state_export<double>((const double2*)c->S, (double2*)uhat, c->n2, c->n3, c->nh, c->P, c->stream)
+                         : hs::launch_state_export<float>((const float2*)c->S, (double2*)uhat, c->n2, c->n3, c->nh, c->P, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state export");
+  return HS_OK;
+}
+
+hs_status hs_set_state(hs_ctx* c, const void* uhat) {
+  if (!c || !uhat) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (c->prec == HS_FP32_REFINED) return fail(c, HS_ERR_INVALID_ARG, "state import is not available in refined mode");
+  cudaError_t e = c->f64 ? hs::launch_state_import<double>((const double2*)uhat, (double2*)c->S, c->n2, c->n3, c->nh, c->P, c->stream)
+                         : hs::launch_state_import<float>((const double2*)uhat, (float2*)c->S, c->n2, c->n3, c->nh, c->P, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state import");
+  c->warm = true;
+  return HS_OK;
+}
+
+hs_status hs_get_reference_medium(const hs_ctx* c, double C0[36]) {
+  if (!c || !C0) return HS_ERR_INVALID_ARG;
+  memcpy(C0, c->C0, sizeof(c->C0));
+  return HS_OK;
+}
+
+hs_status hs_profile_enable(hs_ctx* c, int on) {
+  if (!c) return HS_ERR_INVALID_ARG;
+  c->prof = (on != 0);
+  return HS_OK;
+}
+
+hs_status hs_profile_read(hs_ctx* c, double ms[7], long long launches[7]) {
+  if (!c || !ms || !launches) return HS_ERR_INVALID_ARG;
+  for (int k = 0; k < HS_K_COUNT; ++k) ms[k] = 0;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile read");
+  for (auto& ev : c->ev_used) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess) ms[ev.kind] += t;
+    c->ev_pool.push_back(ev.a);
+    c->ev_pool.push_back(ev.b);
+  }
+  c->ev_used.clear();
+  for (int k = 0; k < HS_K_COUNT; ++k) {
+    launches[k] = c->launches[k];
+    c->launches[k] = 0;
+  }
+  return HS_OK;
+}
+
+void hs_destroy(hs_ctx* c) {
+  if (!c) return;
+  for (auto& ev : c->ev_used) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* hs_error_string(hs_status s) {
+  switch (s) {
+    case HS_OK: return "converged";
+    case HS_NOT_CONVERGED: return "max_iter reached before err < tol";
+    case HS_ERR_INVALID_ARG: return "invalid argument";
+    case HS_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case HS_ERR_OOM: return "workspace too small";
+    case HS_ERR_CUDA: return "CUDA error";
+    case HS_DIVERGED: return "iteration diverged";
+    case HS_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* hs_last_error(const hs_ctx* c) {
+  if (c) return c->last_err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

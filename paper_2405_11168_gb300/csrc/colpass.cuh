@@ -1,0 +1,156 @@
+// Column passes: FFTs along y or z of the half-spectrum fields, and the Green
+// update fused between the forward and inverse z transforms.
+//
+// A block owns CT consecutive x-frequency columns (one 128-byte row segment
+// per component) of one z (y-pass) or one y (z-pass) and all three
+// displacement/force components.  Shared-memory layout [e][comp][col], so
+// every row of the tile is contiguous and each FFT sequence is a column.
+//
+// Green update (Algorithm 1 step 5, with Eq. Green_tensor): at every q,
+//   Dt_i(q) = D_i(q) exp(-i q.(1/2,1/2,1/2)) from the per-axis tables
+//            exp(-i q_x), exp(-i q_y), exp(-i q_z) (corner-indexed state),
+//   M_ik = 2 Re(Dt_i conj(Dt_k)),  Omega^-1_jl = sum_ik lambda0_jikl M_ik,
+//   u(q) <- u(q) - (2/N) Omega(q) F_unnormalised(q),
+// with Omega = 0 and u = 0 at q = 0 and q = (pi,pi,pi) (Section 2.3).
+// The factor 2 is f = 2 F_hat (the force transform equals half the
+// equilibrium residual f of Eq. basic_scheme_dep_2); 1/N is the forward
+// normalisation of Eq. FT, applied here once.
+#pragma once
+#include "common.cuh"
+
+namespace hs {
+
+enum { COL_Y_FWD = 0, COL_Y_INV = 1, COL_Z_GREEN = 2, COL_Z_INV_STATE = 3 };
+
+template <typename T> struct ColArgs {
+  using C = typename cplx_t<T>::type;
+  C* buf;            // [3][n3][n2][P]
+  C* S;              // state u_hat, same layout
+  const C* tw;       // w_L^j of the transformed axis
+  const C* tw1;      // exp(-i q_x) table (= w_N1^h)
+  const C* tw2;
+  const C* tw3;
+  FftPlan plan;
+  int n1, n2, n3, P, nh;
+  T scale;           // 2/N
+  T G6[36];          // Omega^-1 (Voigt pairs) = G6 . M (Voigt pairs)
+  const DevStatus* st;
+  int skip_if_done;
+};
+
+template <typename T>
+__device__ __forceinline__ void green_apply(const ColArgs<T>& a, int h1, int h2, int h3,
+                                            typename cplx_t<T>::type (&F)[3],
+                                            typename cplx_t<T>::type (&U)[3]) {
+  using C = typename cplx_t<T>::type;
+  const bool trans = (h1 == 0 && h2 == 0 && h3 == 0) ||
+                     (2 * h1 == a.n1 && 2 * h2 == a.n2 && 2 * h3 == a.n3);
+  if (trans) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) U[j] = cmk<C>(0, 0);
+    return;
+  }
+  const C ex = __ldg(a.tw1 + h1), ey = __ldg(a.tw2 + h2), ez = __ldg(a.tw3 + h3);
+  const C yz = cmul(ey, ez), xy = cmul(ex, ey), xz = cmul(ex, ez);
+  const T h = T(0.5);
+  // corner-convention symbols (Eq. Dq times exp(-i q.(1/2,1/2,1/2)))
+  C D[3];
+  D[0] = cmk<C>(h * (T(1) + yz.x - xy.x - xz.x), h * (yz.y - xy.y - xz.y));
+  D[1] = cmk<C>(h * (T(1) - yz.x - xy.x + xz.x), h * (-yz.y - xy.y + xz.y));
+  D[2] = cmk<C>(h * (T(1) - yz.x + xy.x - xz.x), h * (-yz.y + xy.y - xz.y));
+  // M in Voigt pair order (11,22,33,23,13,12)
+  T M[6];
+  M[0] = T(2) * (D[0].x * D[0].x + D[0].y * D[0].y);
+  M[1] = T(2) * (D[1].x * D[1].x + D[1].y * D[1].y);
+  M[2] = T(2) * (D[2].x * D[2].x + D[2].y * D[2].y);
+  M[3] = T(2) * (D[1].x * D[2].x + D[1].y * D[2].y);
+  M[4] = T(2) * (D[0].x * D[2].x + D[0].y * D[2].y);
+  M[5] = T(2) * (D[0].x * D[1].x + D[0].y * D[1].y);
+  T A[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += a.G6[i * 6 + j] * M[j];
+    A[i] = s;
+  }
+  // inverse of the symmetric 3x3 [[A0,A5,A4],[A5,A1,A3],[A4,A3,A2]]
+  const T c11 = A[1] * A[2] - A[3] * A[3];
+  const T c22 = A[0] * A[2] - A[4] * A[4];
+  const T c33 = A[0] * A[1] - A[5] * A[5];
+  const T c23 = A[4] * A[5] - A[0] * A[3];
+  const T c13 = A[5] * A[3] - A[1] * A[4];
+  const T c12 = A[4] * A[3] - A[2] * A[5];
+  const T det = A[0] * c11 + A[5] * c12 + A[4] * c13;
+  const T s = a.scale / det;
+  const T O[3][3] = {{c11 * s, c12 * s, c13 * s}, {c12 * s, c22 * s, c23 * s}, {c13 * s, c23 * s, c33 * s}};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    C acc = U[j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc.x -= O[j][k] * F[k].x;
+      acc.y -= O[j][k] * F[k].y;
+    }
+    U[j] = acc;
+  }
+}
+
+template <typename T, int CT, int MODE>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArgs<T> a) {
+  using C = typename cplx_t<T>::type;
+  if (a.skip_if_done && a.st->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);  // [L][3][CT]
+  const bool yaxis = (MODE == COL_Y_FWD || MODE == COL_Y_INV);
+  const int L = yaxis ? a.n2 : a.n3;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int x0 = blockIdx.x * CT;
+  const int outer = blockIdx.y;
+  const int ncol = min(CT, a.nh - x0);
+  const size_t plane = (size_t)a.n2 * a.P;
+  const size_t cstride = (size_t)a.n3 * plane;
+  const size_t rstride = yaxis ? (size_t)a.P : plane;
+  const size_t base = yaxis ? (size_t)outer * plane + x0 : (size_t)outer * a.P + x0;
+  const C* src = (MODE == COL_Z_INV_STATE) ? a.S : a.buf;
+  const FftPlan plan = a.plan;
+  const C* __restrict__ tw = a.tw;
+  constexpr int W = 3 * CT;
+  for (int i = tid; i < L * W; i += nthr) {
+    const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;
+    sm[i] = (col < ncol) ? src[c * cstride + base + e * rstride + col] : cmk<C>(0, 0);
+  }
+  __syncthreads();
+  if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
+    HS_FFT(true, sm, 1, W, W, plan, tw, tid, nthr);
+  } else {
+    HS_FFT(false, sm, 1, W, W, plan, tw, tid, nthr);
+  }
+  if (MODE == COL_Z_GREEN) {
+    for (int i = tid; i < L * CT; i += nthr) {
+      const int z = i / CT, col = i - z * CT;
+      if (col >= ncol) continue;
+      C F[3], U[3];
+      const size_t g = base + z * rstride + col;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        F[c] = sm[z * W + c * CT + col];
+        U[c] = a.S[c * cstride + g];
+      }
+      green_apply<T>(a, x0 + col, outer, z, F, U);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a.S[c * cstride + g] = U[c];
+        sm[z * W + c * CT + col] = U[c];
+      }
+    }
+    __syncthreads();
+    HS_FFT(true, sm, 1, W, W, plan, tw, tid, nthr);
+  }
+  for (int i = tid; i < L * W; i += nthr) {
+    const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;
+    if (col < ncol) a.buf[c * cstride + base + e * rstride + col] = sm[i];
+  }
+}
+
+}  // namespace hs

@@ -1,0 +1,147 @@
+// Shared device-side definitions of the tetrahedral-stencil solver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace hs {
+
+// Device-resident solve status.  Written by the last block of every
+// residual-evaluating kernel (see finalize()); read by every other kernel at
+// entry so that the work queued after convergence becomes a no-op.
+struct DevStatus {
+  int done;       // 0 running, 1 converged, 2 max_iter reached, 3 diverged
+  int evals;      // residual evaluations so far
+  int max_iter;   // stop (done = 2) after this many evaluations
+  int hist_cap;   // capacity of the error history
+  unsigned int counter;  // block-arrival counter of the last-block reduction
+  int pad0;
+  double tol;       // converged when err < tol
+  double err;       // error of the last evaluation, Eq. (tolerance)
+  double l2;        // L2 norm of the nodal force, Eq. (L2-norm)
+  double sig_norm;  // Frobenius norm of <sigma>
+  double sig_mean[6];  // <sigma> = 1/2(<sigma^T1> + <sigma^T2>), Voigt order
+  double err_min;
+  double denom;     // > 0: use this instead of sig_norm (correction solves)
+  double nvox;      // N
+};
+
+enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
+constexpr int NRED = 7;  // sum of sigma^T1 + sigma^T2 (6), sum |F|^2 (1)
+
+// Isotropic phases: per phase (lambda, mu).
+template <typename T> struct MatIso {
+  const T* tab;
+  __device__ __forceinline__ void stress(int ph, const T* e, T* s) const {
+    const T lam = __ldg(tab + 2 * ph), mu = __ldg(tab + 2 * ph + 1);
+    const T lt = lam * (e[0] + e[1] + e[2]);
+    const T m2 = mu + mu;
+    s[0] = lt + m2 * e[0];
+    s[1] = lt + m2 * e[1];
+    s[2] = lt + m2 * e[2];
+    s[3] = mu * e[3];
+    s[4] = mu * e[4];
+    s[5] = mu * e[5];
+  }
+};
+
+// General anisotropic phases: per phase the 21 upper-triangle entries of the
+// 6x6 Voigt stiffness, row-major.  e is the engineering Voigt strain.
+template <typename T> struct MatAniso {
+  const T* tab;
+  __device__ __forceinline__ void stress(int ph, const T* e, T* s) const {
+    const T* c = tab + 21 * ph;
+    T C[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) C[i] = __ldg(c + i);
+    // index of (i,j), i <= j, in the packed upper triangle
+#define HS_UT(i, j) ((i) * 6 - ((i) * ((i) - 1)) / 2 + ((j) - (i)))
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc += C[i <= j ? HS_UT(i, j) : HS_UT(j, i)] * e[j];
+      s[i] = acc;
+    }
+#undef HS_UT
+  }
+};
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-sum NRED doubles (fixed order) and publish them as this block's
+// partials; the last block to arrive reduces all partials in index order and
+// updates the status.  scratch: >= 32 * NRED doubles of shared memory.
+__device__ inline void reduce_and_finalize(const double (&acc)[NRED], double* partials, DevStatus* st,
+                                           double* hist, double* scratch) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  const int nblk = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  __shared__ bool am_last;
+#pragma unroll
+  for (int v = 0; v < NRED; ++v) {
+    double s = warp_sum(acc[v]);
+    if (lane == 0) scratch[warp * NRED + v] = s;
+  }
+  __syncthreads();
+  if (tid < NRED) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += scratch[w * NRED + tid];
+    partials[(size_t)bid * NRED + tid] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int prev = atomicAdd(&st->counter, 1u);
+    am_last = (prev == (unsigned int)(nblk - 1));
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // deterministic: value v by warp (v mod nw), lanes stride over blocks
+  for (int v = warp; v < NRED; v += nw) {
+    double s = 0;
+    for (int b = lane; b < nblk; b += 32) s += __ldcg(partials + (size_t)b * NRED + v);
+    s = warp_sum(s);
+    if (lane == 0) scratch[v] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double n = st->nvox;
+    double sm[6], nrm2 = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      sm[i] = 0.5 * scratch[i] / n;
+      nrm2 += (i < 3 ? 1.0 : 2.0) * sm[i] * sm[i];
+      st->sig_mean[i] = sm[i];
+    }
+    const double l2 = sqrt(scratch[6] / n);
+    const double nrm = sqrt(nrm2);
+    const double den = st->denom > 0 ? st->denom : nrm;
+    double err;
+    if (den > 0) err = l2 / den;
+    else err = (l2 == 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
+    st->l2 = l2;
+    st->sig_norm = nrm;
+    st->err = err;
+    const int k = st->evals;
+    if (k < st->hist_cap) hist[k] = err;
+    st->evals = k + 1;
+    if (!(err == err) || err > 1e300) {
+      st->done = DONE_DIVERGED;
+    } else {
+      if (k == 0 || err < st->err_min) st->err_min = err;
+      if (err < st->tol) st->done = DONE_CONVERGED;
+      else if (err > 1e6 * st->err_min && k > 10) st->done = DONE_DIVERGED;
+      else if (k + 1 >= st->max_iter) st->done = DONE_MAXITER;
+    }
+    st->counter = 0;
+  }
+}
+
+}  // namespace hs

@@ -1,0 +1,217 @@
+// Batched mixed-radix (2/3/4/8/16) complex FFTs on sequences held in shared memory.
+//
+// Self-sorting Stockham formulation, one radix-R butterfly per (thread, step):
+// stage s with radix R and Ns = R_1...R_{s-1} reads x[b + m L/R], multiplies by
+// the twiddle w_{Ns R}^{(b mod Ns) m}, takes a length-R DFT and writes
+// y[(b div Ns) Ns R + (b mod Ns) + m Ns].  After the last stage the result is in
+// natural order.  Every stage is done in place: a thread loads all of its
+// butterflies' inputs into registers, the block synchronises, then it writes.
+//
+// Threads per sequence: ceil(L/kE) with kE = 8 elements per thread, so a
+// thread never holds more than ceil(kE/R) butterflies of one stage; radices
+// are 8, 4, 3 and 2 (a radix-16 DFT is available but keeps too many values
+// live for the generic stage loop).  Sequence s, element e lives at
+// buf[s*ss + e*es].  Forward = exp(-2 pi i nk/L), inverse = exp(+...), both
+// unnormalised.  Twiddles come from a per-axis table w_L^j = exp(-2 pi i j/L),
+// j < L, computed on the host.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace hs {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+// multiply by -i (forward quarter turn) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot90(C a) {
+  return INV ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
+}
+
+// cos and sin of 2 pi J / 16 (exact constants of the regular 16-gon)
+#define HS_FFT_C1 0.92387953251128675613
+#define HS_FFT_S1 0.38268343236508977173
+#define HS_FFT_H 0.70710678118654752440
+__host__ __device__ constexpr double cos16c(int j) {
+  return ((j & 15) == 0) ? 1.0 : ((j & 15) == 1) ? HS_FFT_C1 : ((j & 15) == 2) ? HS_FFT_H : ((j & 15) == 3) ? HS_FFT_S1
+       : ((j & 15) == 4) ? 0.0 : ((j & 15) == 5) ? -HS_FFT_S1 : ((j & 15) == 6) ? -HS_FFT_H : ((j & 15) == 7) ? -HS_FFT_C1
+       : ((j & 15) == 8) ? -1.0 : ((j & 15) == 9) ? -HS_FFT_C1 : ((j & 15) == 10) ? -HS_FFT_H : ((j & 15) == 11) ? -HS_FFT_S1
+       : ((j & 15) == 12) ? 0.0 : ((j & 15) == 13) ? HS_FFT_S1 : ((j & 15) == 14) ? HS_FFT_H : HS_FFT_C1;
+}
+// sin(t) = cos(t + 3 pi / 2)
+__host__ __device__ constexpr double sin16c(int j) { return cos16c(j + 12); }
+// w16^J for the requested direction (forward: exp(-2 pi i J/16))
+template <int J, bool INV, typename C> __device__ __forceinline__ C w16() {
+  using R = decltype(C::x);
+  constexpr double c = cos16c(J), sn = sin16c(J);
+  return cmk<C>((R)c, INV ? (R)sn : (R)-sn);
+}
+
+template <int R, bool INV, typename C> struct Dft;
+
+template <bool INV, typename C> struct Dft<2, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV, typename C> struct Dft<3, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    using R = decltype(C::x);
+    const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+    C s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    C x0 = v[0];
+    C m = cmk<C>(x0.x - (R)0.5 * s.x, x0.y - (R)0.5 * s.y);
+    // forward: X1 = m - i h d, X2 = m + i h d
+    C ihd = cmk<C>(-h * d.y, h * d.x);  // i h d
+    v[0] = cadd(x0, s);
+    if (INV) {
+      v[1] = cadd(m, ihd);
+      v[2] = csub(m, ihd);
+    } else {
+      v[1] = csub(m, ihd);
+      v[2] = cadd(m, ihd);
+    }
+  }
+};
+
+template <bool INV, typename C> struct Dft<4, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    C t2 = cadd(v[1], v[3]), t3 = rot90<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+// composite DFT of length A*B: n = B n1 + n2, k = k1 + A k2
+template <int A, int B, bool INV, typename C, int N2 = 1, int K1 = 1>
+__device__ __forceinline__ void twiddle_all(C (&y)[B][A]) {
+  if constexpr (N2 < B) {
+    if constexpr (K1 < A) {
+      y[N2][K1] = cmul(y[N2][K1], w16<(16 / (A * B)) * N2 * K1, INV, C>());
+      twiddle_all<A, B, INV, C, N2, K1 + 1>(y);
+    } else {
+      twiddle_all<A, B, INV, C, N2 + 1, 1>(y);
+    }
+  }
+}
+
+template <int A, int B, bool INV, typename C> __device__ __forceinline__ void dft_composite(C* v) {
+  C y[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) y[n2][n1] = v[B * n1 + n2];
+    Dft<A, INV, C>::run(y[n2]);
+  }
+  twiddle_all<A, B, INV, C>(y);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    C z[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) z[n2] = y[n2][k1];
+    Dft<B, INV, C>::run(z);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = z[k2];
+  }
+}
+
+template <bool INV, typename C> struct Dft<8, INV, C> {
+  static __device__ __forceinline__ void run(C* v) { dft_composite<2, 4, INV>(v); }
+};
+template <bool INV, typename C> struct Dft<16, INV, C> {
+  static __device__ __forceinline__ void run(C* v) { dft_composite<4, 4, INV>(v); }
+};
+
+constexpr int kMaxStages = 8;
+// Radix of each stage packed 4 bits per stage (stage 0 in the low bits), so
+// the plan is three plain integers and never needs indexed storage.
+struct FftPlan {
+  int L;       // sequence length
+  int nstage;  // number of radix stages (<= kMaxStages)
+  int packed;  // radix of stage s = (packed >> 4 s) & 15, product = L
+};
+
+// One Stockham stage over the sequences handled by this thread.
+constexpr int kE = 8;
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void stockham_stage(C* buf, int ss, int es, int s, int t, int T, bool active,
+                                               int L, int Ns, const C* __restrict__ tw) {
+  constexpr int KB = (kE + R - 1) / R;
+  C v[KB][R];
+  const int nb = L / R;
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int b = t + k * T;
+    if (active && b < nb) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[k][m] = buf[s * ss + (b + m * nb) * es];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int b = t + k * T;
+    if (active && b < nb) {
+      const int kk = b % Ns;
+      if (Ns > 1) {
+        const int step = L / (Ns * R);
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          C w = __ldg(tw + kk * m * step);
+          if (INV) w.y = -w.y;
+          v[k][m] = cmul(v[k][m], w);
+        }
+      }
+      Dft<R, INV, C>::run(v[k]);
+      const int base = (b / Ns) * Ns * R + kk;
+#pragma unroll
+      for (int m = 0; m < R; ++m) buf[s * ss + (base + m * Ns) * es] = v[k][m];
+    }
+  }
+  __syncthreads();
+}
+
+// FFT of nseq sequences in place.  All threads of the block must call this.
+// Thread i works on sequence (g0 + i / T) for each group start g0, where
+// T = ceil(L/kE) threads per sequence and (blockDim / T) sequences per group.
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_smem(C* buf, int ss, int es, int nseq, int L, int nstage, int packed,
+                                         const C* __restrict__ tw, int tid, int nthreads) {
+  const int T = (L + kE - 1) / kE;
+  const int G = nthreads / T;
+  for (int g0 = 0; g0 < nseq; g0 += G) {
+    const int s = g0 + tid / T;
+    const int t = tid % T;
+    const bool active = (tid / T) < G && s < nseq;
+    int Ns = 1;
+#pragma unroll 1
+    for (int st = 0; st < nstage; ++st) {
+      const int R = (packed >> (4 * st)) & 15;
+      if (R == 8) stockham_stage<8, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
+      else if (R == 4) stockham_stage<4, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
+      else if (R == 3) stockham_stage<3, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
+      else stockham_stage<2, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
+      Ns *= R;
+    }
+  }
+}
+
+#define HS_FFT(INV, buf, ss, es, nseq, plan, tw, tid, nthr) \
+  ::hs::fft_smem<INV>(buf, ss, es, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
+
+}  // namespace hs

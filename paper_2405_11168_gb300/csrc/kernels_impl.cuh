@@ -1,0 +1,128 @@
+// Definitions of the launchers in launch.h; included once per precision.
+#pragma once
+#include "launch.h"
+
+namespace hs {
+
+template <typename K> static cudaError_t set_smem(K kernel, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <typename T, int TY, class MAT, int MODE, bool REAL>
+static cudaError_t march_one(const MarchArgs<T>& a, const MAT& m, dim3 g, int nthr, size_t smem, cudaStream_t s) {
+  auto k = k_march<T, TY, MAT, MODE, REAL>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<g, nthr, smem, s>>>(a, m);
+  return cudaGetLastError();
+}
+
+template <typename T, int TY, bool REAL>
+static cudaError_t march_ty(const MarchArgs<T>& a, bool iso, int mode, dim3 g, int nthr, size_t smem,
+                            cudaStream_t s) {
+  if (mode == MODE_EMIT) {
+    if (REAL) return cudaErrorInvalidValue;
+    return march_one<T, TY, MatIso<T>, MODE_EMIT, false>(a, MatIso<T>{a.mat}, g, nthr, smem, s);
+  }
+  if (iso) {
+    MatIso<T> m{a.mat};
+    if (mode == MODE_FORCE) return march_one<T, TY, MatIso<T>, MODE_FORCE, REAL>(a, m, g, nthr, smem, s);
+    return march_one<T, TY, MatIso<T>, MODE_FIELDS, REAL>(a, m, g, nthr, smem, s);
+  }
+  MatAniso<T> m{a.mat};
+  if (mode == MODE_FORCE) return march_one<T, TY, MatAniso<T>, MODE_FORCE, REAL>(a, m, g, nthr, smem, s);
+  return march_one<T, TY, MatAniso<T>, MODE_FIELDS, REAL>(a, m, g, nthr, smem, s);
+}
+
+template <typename T, bool REAL>
+static cudaError_t march_real(const MarchArgs<T>& a, bool iso, int ty, int mode, dim3 g, int nthr, size_t smem,
+                              cudaStream_t s) {
+  switch (ty) {
+    case 2: return march_ty<T, 2, REAL>(a, iso, mode, g, nthr, smem, s);
+    case 4: return march_ty<T, 4, REAL>(a, iso, mode, g, nthr, smem, s);
+    case 8: return march_ty<T, 8, REAL>(a, iso, mode, g, nthr, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int CT, int MODE>
+static cudaError_t col_one(const ColArgs<T>& a, dim3 g, int nthr, size_t smem, cudaStream_t s) {
+  auto k = k_col<T, CT, MODE>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<g, nthr, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int CT>
+static cudaError_t col_ct(const ColArgs<T>& a, int mode, dim3 g, int nthr, size_t smem, cudaStream_t s) {
+  switch (mode) {
+    case COL_Y_FWD: return col_one<T, CT, COL_Y_FWD>(a, g, nthr, smem, s);
+    case COL_Y_INV: return col_one<T, CT, COL_Y_INV>(a, g, nthr, smem, s);
+    case COL_Z_GREEN: return col_one<T, CT, COL_Z_GREEN>(a, g, nthr, smem, s);
+    case COL_Z_INV_STATE: return col_one<T, CT, COL_Z_INV_STATE>(a, g, nthr, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+__global__ void k_state_export(const typename cplx_t<T>::type* S, double2* out, size_t nrows, int nh, int P) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * nh) return;
+  size_t r = i / nh, k = i - r * nh;
+  auto v = S[r * P + k];
+  out[i] = make_double2((double)v.x, (double)v.y);
+}
+
+template <typename T>
+__global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, size_t nrows, int nh, int P) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * P) return;
+  size_t r = i / P, k = i - r * P;
+  typename cplx_t<T>::type v;
+  if ((int)k < nh) {
+    double2 d = in[r * nh + k];
+    v.x = (T)d.x;
+    v.y = (T)d.y;
+  } else {
+    v.x = 0;
+    v.y = 0;
+  }
+  S[i] = v;
+}
+
+}  // namespace hs
+
+#define HS_INSTANTIATE(T, REALOK, CT)                                                                    \
+  namespace hs {                                                                                         \
+  template <>                                                                                            \
+  cudaError_t launch_march<T>(const MarchArgs<T>& a, bool iso, int ty, int mode, bool real, dim3 grid,  \
+                              int nthr, size_t smem, cudaStream_t s) {                                   \
+    if (real) {                                                                                          \
+      if (!(REALOK)) return cudaErrorInvalidValue;                                                       \
+      return march_real<T, REALOK>(a, iso, ty, mode, grid, nthr, smem, s);                               \
+    }                                                                                                    \
+    return march_real<T, false>(a, iso, ty, mode, grid, nthr, smem, s);                                  \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_col<T>(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem,      \
+                            cudaStream_t s) {                                                            \
+    if (ct != (CT)) return cudaErrorInvalidValue;                                                        \
+    return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                                  \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_state_export<T>(const typename cplx_t<T>::type* S, double2* out, int n2, int n3,     \
+                                     int nh, int P, cudaStream_t s) {                                    \
+    size_t nrows = (size_t)3 * n3 * n2, n = nrows * nh;                                                  \
+    k_state_export<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, out, nrows, nh, P);                 \
+    return cudaGetLastError();                                                                           \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_state_import<T>(const double2* in, typename cplx_t<T>::type* S, int n2, int n3,      \
+                                     int nh, int P, cudaStream_t s) {                                    \
+    size_t nrows = (size_t)3 * n3 * n2, n = nrows * P;                                                   \
+    k_state_import<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, S, nrows, nh, P);                  \
+    return cudaGetLastError();                                                                           \
+  }                                                                                                      \
+  }

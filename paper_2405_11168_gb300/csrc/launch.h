@@ -1,0 +1,32 @@
+// Internal launch interface between the C-ABI host code and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "colpass.cuh"
+#include "march.cuh"
+
+namespace hs {
+
+// mode: MODE_FORCE / MODE_FIELDS / MODE_EMIT; real: input is the FP64 real
+// displacement field (only for T = double).
+template <typename T>
+cudaError_t launch_march(const MarchArgs<T>& a, bool iso, int ty, int mode, bool real, dim3 grid, int nthr,
+                         size_t smem, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_col(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
+
+// u8 phase ids -> u16
+cudaError_t launch_ids_u8_to_u16(const uint8_t* in, uint16_t* out, size_t n, cudaStream_t s);
+// largest id into *out (int, must start at 0)
+cudaError_t launch_max_id(const uint16_t* ids, size_t n, int* out, cudaStream_t s);
+// padded T-complex state <-> packed complex128 [3][n3][n2][nh]
+template <typename T>
+cudaError_t launch_state_export(const typename cplx_t<T>::type* S, double2* out, int n2, int n3, int nh, int P,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_state_import(const double2* in, typename cplx_t<T>::type* S, int n2, int n3, int nh, int P,
+                                cudaStream_t s);
+
+}  // namespace hs

@@ -1,0 +1,241 @@
+"""Thin ctypes binding of the C ABI in ``include/hs.h`` (argument marshalling only).
+
+Every function here forwards to the function of the same name in
+``libhs.so``; all arithmetic runs in the library's CUDA kernels.  Loading
+fails loudly when the library has not been built.
+
+``Solver`` is a convenience wrapper that allocates the workspace as a PyTorch
+tensor (PyTorch provides device memory and the stream) and calls
+``hs_create`` / ``hs_solve`` / ``hs_destroy``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhs.so")
+
+HS_OK = 0
+HS_NOT_CONVERGED = 1
+HS_ERR_INVALID_ARG = -1
+HS_ERR_UNSUPPORTED_SIZE = -2
+HS_ERR_OOM = -3
+HS_ERR_CUDA = -4
+HS_DIVERGED = -5
+HS_ERR_TIMEOUT = -6
+
+HS_FP64, HS_FP32, HS_FP32_REFINED = 0, 1, 2
+KERNEL_CLASSES = ["xpass", "y_fwd", "z_green", "y_inv", "resid64", "fields", "other"]
+HS_IDS_U8, HS_IDS_U16 = 0, 1
+
+# every exported function of include/hs.h
+EXPORTS = [
+    "hs_default_options",
+    "hs_workspace_size",
+    "hs_create",
+    "hs_solve",
+    "hs_err_history",
+    "hs_get_state",
+    "hs_set_state",
+    "hs_get_reference_medium",
+    "hs_profile_enable",
+    "hs_profile_read",
+    "hs_destroy",
+    "hs_error_string",
+    "hs_last_error",
+]
+
+
+class hs_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ids", ctypes.c_void_p),
+                ("table", ctypes.POINTER(ctypes.c_double)), ("nphase", ctypes.c_int)]
+
+
+class hs_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("out_f32", ctypes.c_int),
+                ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double)]
+
+
+class HSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libhs.so`` (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    dptr = ctypes.POINTER(ctypes.c_double)
+    iptr = ctypes.POINTER(ctypes.c_int)
+    lib.hs_default_options.argtypes = [ctypes.POINTER(hs_options)]
+    lib.hs_workspace_size.argtypes = [ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(hs_options),
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.hs_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
+                              dptr, ctypes.POINTER(hs_options), P, ctypes.c_size_t, P]
+    lib.hs_solve.argtypes = [P, dptr, D, I, P, P, dptr, iptr, dptr]
+    lib.hs_err_history.argtypes = [P, dptr, I, iptr]
+    lib.hs_get_state.argtypes = [P, P]
+    lib.hs_set_state.argtypes = [P, P]
+    lib.hs_get_reference_medium.argtypes = [P, dptr]
+    lib.hs_profile_enable.argtypes = [P, I]
+    lib.hs_profile_read.argtypes = [P, dptr, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hs_destroy.argtypes = [P]
+    lib.hs_destroy.restype = None
+    lib.hs_error_string.argtypes = [I]
+    lib.hs_error_string.restype = ctypes.c_char_p
+    lib.hs_last_error.argtypes = [P]
+    lib.hs_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("hs_destroy", "hs_error_string", "hs_last_error"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(lib, s, ctx=None):
+    if s < 0:
+        msg = lib.hs_last_error(ctx).decode() if ctx is not None else lib.hs_last_error(None).decode()
+        raise HSError(s, f"{lib.hs_error_string(s).decode()}: {msg}")
+    return s
+
+
+def default_options(**kw):
+    lib = load()
+    o = hs_options()
+    lib.hs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def workspace_size(grid, nphase, opt):
+    lib = load()
+    g = (ctypes.c_int * 3)(*grid)
+    n = ctypes.c_size_t()
+    _check(lib, lib.hs_workspace_size(g, int(nphase), ctypes.byref(opt), ctypes.byref(n)))
+    return n.value
+
+
+class Solver:
+    """One microstructure on one device (thin wrapper over hs_create / hs_solve)."""
+
+    def __init__(self, ids, table, C0=None, precision=HS_FP64, device="cuda", stream=None, **optkw):
+        import torch
+
+        self.lib = load()
+        self.torch = torch
+        ids_t = ids if isinstance(ids, torch.Tensor) else None
+        shape = tuple(ids.shape)
+        self.grid = (shape[2], shape[1], shape[0])
+        self.N = int(np.prod(shape))
+        table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
+        self.nphase = table.shape[0]
+        self.opt = default_options(precision=precision, **optkw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        nbytes = workspace_size(self.grid, self.nphase, self.opt)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        if ids_t is None:
+            ids_np = np.ascontiguousarray(ids)
+            kind = HS_IDS_U8 if ids_np.dtype == np.uint8 else HS_IDS_U16
+            ids_np = ids_np.astype(np.uint8 if kind == HS_IDS_U8 else np.uint16, copy=False)
+            ids_ptr = ids_np.ctypes.data
+            self._ids_keep = ids_np
+        else:
+            kind = HS_IDS_U8 if ids_t.dtype == torch.uint8 else HS_IDS_U16
+            ids_ptr = ids_t.data_ptr()
+            self._ids_keep = ids_t
+        self._table = table
+        m = hs_material(kind, ctypes.c_void_p(ids_ptr), _dp(table), self.nphase)
+        c0 = None if C0 is None else np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(36))
+        self._c0 = c0
+        ctx = ctypes.c_void_p()
+        g = (ctypes.c_int * 3)(*self.grid)
+        s = self.lib.hs_create(ctypes.byref(ctx), g, ctypes.byref(m), None if c0 is None else _dp(c0),
+                               ctypes.byref(self.opt), ctypes.c_void_p(self._ws_ptr), ctypes.c_size_t(nbytes),
+                               ctypes.c_void_p(self.stream.cuda_stream))
+        _check(self.lib, s)
+        self.ctx = ctx
+
+    def solve(self, E, tol=1e-8, max_iter=1000, fields=True):
+        """Returns dict(status, iters, err, sig_eff, eps, sig); eps/sig are torch tensors [6,N3,N2,N1]."""
+        torch = self.torch
+        E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(6))
+        eps = sig = None
+        if fields:
+            dt = torch.float32 if self.opt.out_f32 else torch.float64
+            shp = (6, self.grid[2], self.grid[1], self.grid[0])
+            eps = torch.empty(shp, dtype=dt, device=self.workspace.device)
+            sig = torch.empty(shp, dtype=dt, device=self.workspace.device)
+        sig_eff = np.zeros(6)
+        iters = ctypes.c_int()
+        err = ctypes.c_double()
+        s = self.lib.hs_solve(self.ctx, _dp(E), float(tol), int(max_iter),
+                              ctypes.c_void_p(eps.data_ptr() if fields else 0),
+                              ctypes.c_void_p(sig.data_ptr() if fields else 0),
+                              _dp(sig_eff), ctypes.byref(iters), ctypes.byref(err))
+        _check(self.lib, s, self.ctx)
+        return dict(status=s, iters=iters.value, err=err.value, sig_eff=sig_eff, eps=eps, sig=sig)
+
+    def err_history(self, n=1 << 16):
+        out = np.zeros(n)
+        k = ctypes.c_int()
+        _check(self.lib, self.lib.hs_err_history(self.ctx, _dp(out), n, ctypes.byref(k)), self.ctx)
+        return out[: k.value]
+
+    def get_state(self):
+        torch = self.torch
+        n1, n2, n3 = self.grid
+        out = torch.empty((3, n3, n2, n1 // 2 + 1), dtype=torch.complex128, device=self.workspace.device)
+        _check(self.lib, self.lib.hs_get_state(self.ctx, ctypes.c_void_p(out.data_ptr())), self.ctx)
+        return out
+
+    def set_state(self, uhat):
+        uhat = uhat.contiguous()
+        self._state_keep = uhat
+        _check(self.lib, self.lib.hs_set_state(self.ctx, ctypes.c_void_p(uhat.data_ptr())), self.ctx)
+
+    def reference_medium(self):
+        out = np.zeros(36)
+        _check(self.lib, self.lib.hs_get_reference_medium(self.ctx, _dp(out)), self.ctx)
+        return out.reshape(6, 6)
+
+    def profile(self, on=True):
+        _check(self.lib, self.lib.hs_profile_enable(self.ctx, int(on)), self.ctx)
+
+    def profile_read(self):
+        """{class: (ms, launches)} since the last read."""
+        ms = np.zeros(7)
+        n = (ctypes.c_longlong * 7)()
+        _check(self.lib, self.lib.hs_profile_read(self.ctx, _dp(ms), n), self.ctx)
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.hs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

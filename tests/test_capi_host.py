@@ -1,0 +1,95 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads,
+exports every function that include/hs.h declares, and rejects bad input
+before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2405_11168_gb300 import build, hs
+
+    build.build()
+    return hs.load()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "hs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    from paper_2405_11168_gb300 import hs
+
+    assert _declared_functions() == sorted(hs.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_default_options_and_status_strings(lib):
+    from paper_2405_11168_gb300 import hs
+
+    o = hs.default_options()
+    assert (o.precision, o.check_every, o.out_f32, o.inner_max) == (hs.HS_FP64, 8, 0, 200)
+    assert o.inner_ratio == pytest.approx(1e-3)
+    for s in range(-6, 2):
+        assert lib.hs_error_string(s)
+
+
+@pytest.mark.parametrize("grid,ok", [((32, 32, 32), True), ((48, 24, 12), True), ((6, 4, 8), True),
+                                     ((31, 32, 32), False), ((2, 4, 4), False), ((40, 32, 32), False),
+                                     ((1024, 32, 32), False), ((44, 44, 44), False)])
+def test_workspace_size_validates_grid(lib, grid, ok):
+    from paper_2405_11168_gb300 import hs
+
+    if ok:
+        n = hs.workspace_size(grid, 2, hs.default_options())
+        nh = grid[0] // 2 + 1
+        assert n >= 3 * 3 * grid[1] * grid[2] * nh * 16   # three complex128 state-sized buffers
+    else:
+        with pytest.raises(hs.HSError) as e:
+            hs.workspace_size(grid, 2, hs.default_options())
+        assert e.value.status == hs.HS_ERR_UNSUPPORTED_SIZE
+
+
+def test_create_rejects_bad_arguments_before_any_device_work(lib):
+    from paper_2405_11168_gb300 import hs
+
+    ids = np.zeros((8, 8, 8), dtype=np.uint8)
+    table = np.eye(6).reshape(1, 36).copy()
+    ctx = ctypes.c_void_p()
+    opt = hs.default_options()
+    grid = (ctypes.c_int * 3)(8, 8, 7)
+    m = hs.hs_material(hs.HS_IDS_U8, ctypes.c_void_p(ids.ctypes.data),
+                       table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1)
+    fake_ws = ctypes.c_void_p(1 << 20)   # never dereferenced: validation fails first
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(m), None, ctypes.byref(opt), fake_ws, 1 << 30, None)
+    assert s == hs.HS_ERR_UNSUPPORTED_SIZE
+    grid = (ctypes.c_int * 3)(8, 8, 8)
+    bad = table.reshape(6, 6).copy()
+    bad[0, 1] = 1.0                      # not symmetric
+    mb = hs.hs_material(hs.HS_IDS_U8, ctypes.c_void_p(ids.ctypes.data),
+                        bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1)
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(mb), None, ctypes.byref(opt), fake_ws, 1 << 30, None)
+    assert s == hs.HS_ERR_INVALID_ARG
+    o2 = hs.default_options(precision=7)
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(m), None, ctypes.byref(o2), fake_ws, 1 << 30, None)
+    assert s == hs.HS_ERR_INVALID_ARG
+    unaligned = ctypes.c_void_p((1 << 20) + 8)
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(m), None, ctypes.byref(opt), unaligned, 1 << 30, None)
+    assert s == hs.HS_ERR_INVALID_ARG
+    C0 = -np.eye(6)                      # not positive definite
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(m), C0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      ctypes.byref(opt), fake_ws, 1 << 30, None)
+    assert s == hs.HS_ERR_INVALID_ARG
+    assert ctx.value is None

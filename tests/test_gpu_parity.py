@@ -1,0 +1,203 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances: FP64 path 1e-10 relative L2 on the fields; FP32 path 1e-5
+(FP32 rounding of a contraction over ~10^2 terms); refined path: the stated
+equilibrium tolerance.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import tetra as T
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_11168_gb300 import build, hs as _hs
+
+    build.build()
+    _hs.load()
+    return _hs
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def voigt_fields(r):
+    return T.voigt_from_tensor(r.eps), T.voigt_from_tensor(r.sig)
+
+
+def sphere_case(grid=(32, 32, 32), contrast=10.0):
+    ids = synth.centred_sphere(grid, volume_fraction=0.2)
+    table = synth.two_phase_table(1.0, 0.3, contrast, 0.3)
+    return ids, table
+
+
+E11 = np.array([1e-3, 0, 0, 0, 0, 0])
+E_MIX = np.array([1e-3, -2e-4, 5e-4, 3e-4, -1e-4, 2e-3])
+
+
+def test_fp64_sphere_iterate_by_iterate(hs):
+    """32^3 centred sphere (f = 0.2), E_i/E_m = 10, nu = 0.3, paper's C0 rule,
+    E11 = 1e-3, tol 1e-8: same iteration count, same error history, same fields."""
+    ids, table = sphere_case()
+    s = hs.Solver(ids, table, precision=hs.HS_FP64)
+    out = s.solve(E11, tol=1e-8, max_iter=1000)
+    hist = s.err_history()
+    lam0 = T.c0_alpha_rule(table)
+    np.testing.assert_allclose(s.reference_medium(), np.array(
+        [[lam0[T._PAIRS[I][0], T._PAIRS[I][1], T._PAIRS[J][0], T._PAIRS[J][1]] for J in range(6)]
+         for I in range(6)]), rtol=1e-14)
+    ref = T.solve_alg1(ids, table, lam0, T.strain_tensor_from_voigt(E11), tol=1e-8, max_iter=1000)
+    assert out["status"] == hs.HS_OK
+    assert out["iters"] == ref.iters
+    np.testing.assert_allclose(hist, ref.errs, rtol=1e-9, atol=1e-14)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-10
+    assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-10
+    se = T.voigt_from_tensor(ref.sig_mean)
+    np.testing.assert_allclose(out["sig_eff"], se, rtol=0, atol=1e-10 * np.abs(se).max())
+
+
+@pytest.mark.parametrize("grid", [(24, 18, 12), (12, 16, 18), (6, 4, 8), (4, 4, 4)])
+def test_fp64_anisotropic_ragged_grids(hs, grid):
+    """Non-cubic grids with radix-3 factors and ragged column tiles; 3 rotated
+    cubic phases; fixed number of evaluations compared field by field."""
+    ids = synth.random_phase_map(grid, 3, seed=sum(grid))
+    table = synth.polycrystal_table(168.4, 121.4, 75.4, synth.random_rotations(3, seed=5))
+    lam0_v = synth.isotropic_voigt(120.0, 0.3)
+    s = hs.Solver(ids, table, C0=lam0_v, precision=hs.HS_FP64)
+    out = s.solve(E_MIX, tol=0.0, max_iter=7)
+    assert out["status"] == hs.HS_NOT_CONVERGED and out["iters"] == 7
+    ref = T.solve_alg1(ids, table, T.stiffness_tensor(lam0_v), T.strain_tensor_from_voigt(E_MIX),
+                       tol=0.0, max_iter=7)
+    np.testing.assert_allclose(s.err_history(), ref.errs, rtol=1e-9)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-10
+    assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-10
+
+
+def _corner_state_to_paper(uc, grid):
+    n1, n2, n3 = grid
+    q1, q2, q3 = T.q_vectors(grid)
+    return uc * np.exp(-0.5j * (q1 + q2 + q3))[None]
+
+
+def test_fp64_evaluation_at_random_state(hs):
+    """A random displacement state loaded through hs_set_state: one evaluation
+    (inverse transforms + stencil + constitutive step) and one update (forward
+    transforms + Green operator) match the oracle's Algorithm 1 from the same state."""
+    grid = (16, 12, 18)
+    ids = synth.random_phase_map(grid, 2, seed=3)
+    table = synth.two_phase_table(2.0, 0.25, 0.0, 0.3)       # with voids
+    C0 = synth.isotropic_voigt(1.5, 0.25)
+    rng = np.random.default_rng(0)
+    u_r = 1e-3 * rng.standard_normal((3, grid[2], grid[1], grid[0]))
+    uc = np.fft.rfftn(u_r, axes=(1, 2, 3)) / np.prod(grid)      # corner-indexed u(q)
+    s = hs.Solver(ids, table, C0=C0, precision=hs.HS_FP64)
+    for n_eval in (1, 2, 3):
+        s.set_state(torch.from_numpy(uc.copy()).cuda())
+        out = s.solve(E_MIX, tol=0.0, max_iter=n_eval)
+        ref = T.solve_alg1(ids, table, T.stiffness_tensor(C0), T.strain_tensor_from_voigt(E_MIX), tol=0.0,
+                           max_iter=n_eval, u0=_corner_state_to_paper(uc, grid))
+        e_ref, s_ref = voigt_fields(ref)
+        assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-11
+        assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-11
+        np.testing.assert_allclose(s.err_history(), ref.errs, rtol=1e-10)
+        st = s.get_state().cpu().numpy()
+        np.testing.assert_allclose(_corner_state_to_paper(st, grid), ref.u_q, atol=1e-12 * np.abs(ref.u_q).max())
+
+
+def test_homogeneous_medium_one_evaluation(hs):
+    grid = (8, 12, 6)
+    ids = np.zeros((grid[2], grid[1], grid[0]), dtype=np.uint8)
+    table = synth.isotropic_voigt(3.0, 0.2)[None]
+    for prec in (hs.HS_FP64, hs.HS_FP32):
+        s = hs.Solver(ids, table, C0=synth.isotropic_voigt(5.0, 0.3), precision=prec)
+        out = s.solve(E_MIX, tol=1e-12, max_iter=50)
+        assert out["status"] == hs.HS_OK and out["iters"] == 1 and out["err"] < (1e-6 if prec else 1e-14)
+        want = np.broadcast_to(E_MIX[:, None, None, None], out["eps"].shape)
+        np.testing.assert_allclose(out["eps"].cpu().numpy(), want, rtol=1e-6 if prec else 1e-15)
+        np.testing.assert_allclose(out["sig_eff"], table[0] @ (E_MIX * [1, 1, 1, 2, 2, 2]),
+                                   rtol=1e-6 if prec else 1e-14)
+
+
+def test_laminate_effective_stiffness_closed_form(hs):
+    from tests.test_oracle_solver import _laminate_closed_form
+
+    grid = (16, 4, 4)
+    layers = [0] * 5 + [1] * 7 + [0] * 2 + [1] * 2
+    ids = synth.laminate_x(grid, layers)
+    table = synth.two_phase_table(1.0, 0.3, 7.0, 0.2)
+    s = hs.Solver(ids, table, C0=synth.isotropic_voigt(8.0, 0.25), precision=hs.HS_FP64)
+    C = np.zeros((6, 6))
+    for J in range(6):
+        E = np.zeros(6)
+        E[J] = 1.0 if J < 3 else 0.5
+        C[:, J] = s.solve(E, tol=1e-12, max_iter=2000, fields=False)["sig_eff"]
+    f1 = np.mean(layers)
+    want = _laminate_closed_form(table, [1 - f1, f1])
+    np.testing.assert_allclose(C, want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
+
+
+def test_fp32_path_within_1e5_of_fp64_oracle(hs):
+    ids, table = sphere_case()
+    s = hs.Solver(ids, table, precision=hs.HS_FP32)
+    out = s.solve(E11, tol=1e-6, max_iter=1000)
+    hist = s.err_history()
+    assert out["status"] == hs.HS_OK, (out["iters"], hist[::20], hist[-5:])
+    ref = T.solve_alg1(ids, table, T.c0_alpha_rule(table), T.strain_tensor_from_voigt(E11), tol=1e-12,
+                       max_iter=2000)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-5
+    assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-5
+
+
+@pytest.mark.parametrize("contrast", [1e3, 1e-3, 0.0])
+def test_refined_path_reaches_fp64_equilibrium(hs, contrast):
+    """FP32 iterations + FP64 residual sweeps: err (FP64) <= 1e-8 and the fields
+    match the FP64 oracle's equilibrium, including voids (C = 0)."""
+    ids, table = sphere_case((24, 24, 24), contrast)
+    s = hs.Solver(ids, table, precision=hs.HS_FP32_REFINED)
+    out = s.solve(E11, tol=1e-8, max_iter=5000)
+    assert out["status"] == hs.HS_OK and out["err"] < 1e-8
+    ref = T.solve_alg1(ids, table, T.c0_alpha_rule(table), T.strain_tensor_from_voigt(E11), tol=1e-12,
+                       max_iter=5000)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-6
+    assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-6
+
+
+def test_error_paths(hs):
+    ids, table = sphere_case((8, 8, 8))
+    s = hs.Solver(ids, table, precision=hs.HS_FP64)
+    with pytest.raises(hs.HSError) as e:
+        s.solve(np.zeros(6))
+    assert e.value.status == hs.HS_ERR_INVALID_ARG
+    with pytest.raises(hs.HSError) as e:
+        s.solve(E11, tol=-1.0)
+    assert e.value.status == hs.HS_ERR_INVALID_ARG
+    bad = ids.copy()
+    bad[0, 0, 0] = 5
+    with pytest.raises(hs.HSError) as e:
+        hs.Solver(bad, table)
+    assert e.value.status == hs.HS_ERR_INVALID_ARG
+    out = s.solve(E11, tol=1e-30, max_iter=3)
+    assert out["status"] == hs.HS_NOT_CONVERGED and out["iters"] == 3
+
+
+def test_deterministic_repeat(hs):
+    ids, table = sphere_case((16, 16, 16))
+    s = hs.Solver(ids, table, precision=hs.HS_FP32)
+    a = s.solve(E_MIX, tol=1e-6, max_iter=300)
+    b = s.solve(E_MIX, tol=1e-6, max_iter=300)
+    assert a["iters"] == b["iters"]
+    assert torch.equal(a["sig"], b["sig"]) and torch.equal(a["eps"], b["eps"])
+    assert np.array_equal(a["sig_eff"], b["sig_eff"])
