@@ -68,10 +68,12 @@ typedef struct {
   int inner_max;        /* HS_FP32_REFINED: max FP32 iterations per correction solve */
   double inner_ratio;   /* HS_FP32_REFINED: a correction solve stops when its force norm is
                            below inner_ratio times the FP64 residual's */
+  int zchunk;           /* z planes per block of the x-pass (0 = automatic; a tiling knob that
+                           does not change results beyond rounding order) */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
- * inner_max 200, inner_ratio 1e-3. */
+ * inner_max 200, inner_ratio 1e-3, zchunk 0. */
 hs_status hs_default_options(hs_options* opt);
 
 /* Device workspace (bytes) that hs_create needs for this grid, precision and

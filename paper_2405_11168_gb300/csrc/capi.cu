@@ -620,6 +620,7 @@ hs_status hs_default_options(hs_options* opt) {
   opt->out_f32 = 0;
   opt->inner_max = 200;
   opt->inner_ratio = 1e-3;
+  opt->zchunk = 0;
   return HS_OK;
 }
 
@@ -644,7 +645,7 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   hs_default_options(&o);
   if (opt) o = *opt;
   if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED || o.check_every < 1 || o.inner_max < 1 ||
-      !(o.inner_ratio > 0 && o.inner_ratio < 1))
+      !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0)
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > 65536)
@@ -760,6 +761,7 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   const int ytiles = c->n2 / c->ty;
   int nzc = std::max(1, std::min(c->n3, (kTargetBlocks + ytiles - 1) / ytiles));
   c->zc = (c->n3 + nzc - 1) / nzc;
+  if (o.zchunk > 0) c->zc = std::min(o.zchunk, c->n3);
   nzc = (c->n3 + c->zc - 1) / c->zc;
   c->grid_m = dim3(ytiles, nzc);
   c->ct = c->f64 ? 8 : 16;

@@ -56,7 +56,7 @@ class hs_material(ctypes.Structure):
 
 class hs_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("out_f32", ctypes.c_int),
-                ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double)]
+                ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double), ("zchunk", ctypes.c_int)]
 
 
 class HSError(RuntimeError):

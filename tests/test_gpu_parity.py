@@ -84,6 +84,25 @@ def test_fp64_anisotropic_ragged_grids(hs, grid):
     assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-10
 
 
+@pytest.mark.parametrize("prec,zchunk", [(0, 1), (0, 3), (0, 7), (1, 5), (1, 16)])
+def test_z_chunking_and_column_groups(hs, prec, zchunk):
+    """Blocks marching over several z planes (zchunk > 1, with a ragged last
+    chunk) and 64^3 column passes with several FFT groups per block give the
+    same iterates as the oracle."""
+    grid = (64, 48, 36)
+    ids = synth.random_phase_map(grid, 2, seed=11)
+    table = synth.two_phase_table(1.0, 0.3, 5.0, 0.3)
+    C0 = synth.isotropic_voigt(3.5, 0.3)
+    s = hs.Solver(ids, table, C0=C0, precision=prec, zchunk=zchunk)
+    out = s.solve(E_MIX, tol=0.0, max_iter=4)
+    ref = T.solve_alg1(ids, table, T.stiffness_tensor(C0), T.strain_tensor_from_voigt(E_MIX), tol=0.0, max_iter=4)
+    tol = 1e-10 if prec == 0 else 2e-5
+    np.testing.assert_allclose(s.err_history(), ref.errs, rtol=tol)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < tol
+    assert rel(out["sig"].cpu().numpy(), s_ref) < tol
+
+
 def _corner_state_to_paper(uc, grid):
     n1, n2, n3 = grid
     q1, q2, q3 = T.q_vectors(grid)
@@ -111,8 +130,12 @@ def test_fp64_evaluation_at_random_state(hs):
         assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-11
         assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-11
         np.testing.assert_allclose(s.err_history(), ref.errs, rtol=1e-10)
-        st = s.get_state().cpu().numpy()
-        np.testing.assert_allclose(_corner_state_to_paper(st, grid), ref.u_q, atol=1e-12 * np.abs(ref.u_q).max())
+        # translation modes (q = 0, q = (pi,pi,pi)) carry no strain: an update
+        # zeroes them in the library (Section 2.4, end) and leaves them in the
+        # oracle; the state is unique elsewhere
+        st = _corner_state_to_paper(s.get_state().cpu().numpy(), grid)
+        keep = ~T.translation_modes(grid)
+        np.testing.assert_allclose(st[:, keep], ref.u_q[:, keep], atol=1e-12 * np.abs(ref.u_q).max())
 
 
 def test_homogeneous_medium_one_evaluation(hs):
@@ -121,7 +144,7 @@ def test_homogeneous_medium_one_evaluation(hs):
     table = synth.isotropic_voigt(3.0, 0.2)[None]
     for prec in (hs.HS_FP64, hs.HS_FP32):
         s = hs.Solver(ids, table, C0=synth.isotropic_voigt(5.0, 0.3), precision=prec)
-        out = s.solve(E_MIX, tol=1e-12, max_iter=50)
+        out = s.solve(E_MIX, tol=1e-6 if prec else 1e-12, max_iter=50)
         assert out["status"] == hs.HS_OK and out["iters"] == 1 and out["err"] < (1e-6 if prec else 1e-14)
         want = np.broadcast_to(E_MIX[:, None, None, None], out["eps"].shape)
         np.testing.assert_allclose(out["eps"].cpu().numpy(), want, rtol=1e-6 if prec else 1e-15)
@@ -148,9 +171,10 @@ def test_laminate_effective_stiffness_closed_form(hs):
 
 
 def test_fp32_path_within_1e5_of_fp64_oracle(hs):
+    """Plain FP32 iterations stop at err < 1e-5 (their rounding floor is a few 1e-6)."""
     ids, table = sphere_case()
     s = hs.Solver(ids, table, precision=hs.HS_FP32)
-    out = s.solve(E11, tol=1e-6, max_iter=1000)
+    out = s.solve(E11, tol=1e-5, max_iter=1000)
     hist = s.err_history()
     assert out["status"] == hs.HS_OK, (out["iters"], hist[::20], hist[-5:])
     ref = T.solve_alg1(ids, table, T.c0_alpha_rule(table), T.strain_tensor_from_voigt(E11), tol=1e-12,
