@@ -151,6 +151,38 @@ hs_status hs_profile_enable(hs_ctx* c, int on);
  * Launch counts are kept whether or not timing is enabled. */
 hs_status hs_profile_read(hs_ctx* c, double ms[7], long long launches[7]);
 
+/* Limits of hs_residual_noalloc's fixed scratch array. */
+#define HS_NOALLOC_SCRATCH_BYTES (512 * 1024) /* bytes held on every device that loads the library */
+#define HS_NOALLOC_MAX_PHASES 1024            /* phases the array can hold */
+#define HS_NOALLOC_MAX_BLOCKS 4096            /* per-block partial sums the array can hold */
+
+/* Equilibrium residual of a displacement field, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a library convenience.  It is for code that must not
+ * allocate at the moment it runs - work being recorded into a CUDA stream capture, real-time or
+ * embedded callers with a fixed memory budget, callers whose device memory belongs entirely to
+ * another allocator - and who therefore cannot supply hs_create's workspace.  It computes, in
+ * FP64, the nodal force F = dE/du of the tetrahedral-stencil energy at the real-space corner
+ * displacement u (the residual of Algorithm 1 evaluated in real space), the mean stress <sigma>
+ * and the L2 norm of F (Eq. L2-norm, real-space form), exactly as the FP64 residual sweep of
+ * HS_FP32_REFINED does.
+ *  grid       N1, N2, N3 as for hs_create.
+ *  ids        device, uint16 phase ids [N3][N2][N1].
+ *  table      host, nphase x 36 Voigt stiffness (as hs_material.table); 1 <= nphase <= HS_NOALLOC_MAX_PHASES.
+ *  E          host, macroscopic strain (tensor components, Voigt order).
+ *  u          device, FP64 [3][N3][N2][N1]: u_k of the corner (l+1/2, m+1/2, n+1/2) at index (l, m, n).
+ *  force      device, float [3][N3][N2][N1], or NULL.
+ *  sig_mean   host, 6: <sigma> = 1/2(<sigma^T1> + <sigma^T2>).      l2: host, sqrt(1/N sum |F|^2).
+ *  stream     cudaStream_t (NULL = legacy default stream); the call returns after its results are on the host.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its scratch is one file-scope
+ * device array of HS_NOALLOC_SCRATCH_BYTES, held by every device that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address (with the device current), so
+ * make that first call before any stream capture.  All calls share the array and each call resets what
+ * must start from zero; calls that overlap on the GPU (other streams, other host threads) race on it.
+ * Sizes beyond the limits above return HS_ERR_INVALID_ARG (phases) or HS_ERR_UNSUPPORTED_SIZE (grid). */
+hs_status hs_residual_noalloc(const int grid[3], const unsigned short* ids, const double* table, int nphase,
+                              const double E[6], const double* u, float* force, double sig_mean[6],
+                              double* l2, void* stream);
+
 /* Release the context (the workspace stays the caller's). */
 void hs_destroy(hs_ctx* c);
 

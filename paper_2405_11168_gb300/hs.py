@@ -43,6 +43,7 @@ EXPORTS = [
     "hs_get_reference_medium",
     "hs_profile_enable",
     "hs_profile_read",
+    "hs_residual_noalloc",
     "hs_destroy",
     "hs_error_string",
     "hs_last_error",
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.hs_get_reference_medium.argtypes = [P, dptr]
     lib.hs_profile_enable.argtypes = [P, I]
     lib.hs_profile_read.argtypes = [P, dptr, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hs_residual_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), P, dptr, I, dptr, P, P, dptr, dptr, P]
     lib.hs_destroy.argtypes = [P]
     lib.hs_destroy.restype = None
     lib.hs_error_string.argtypes = [I]
