@@ -147,8 +147,12 @@ def algorithmic_bytes(kind, grid, refined=True):
     N = n1 * n2 * n3
     nh = n1 // 2 + 1
     comp = n3 * n2 * nh * 8           # one FP32 complex half-spectrum component
-    if kind == "xpass":
-        return 2 * 3 * comp + 2 * N + (3 * N * 4 if refined else 0)
+    if kind == "xpass":               # real-space stencil: u in, ids, correction source, force out
+        return 3 * N * 4 + 2 * N + (3 * N * 4 if refined else 0) + 3 * N * 4
+    if kind == "x_inv":
+        return 3 * comp + 3 * N * 4
+    if kind == "x_fwd":
+        return 3 * N * 4 + 3 * comp
     if kind in ("y_fwd", "y_inv"):
         return 2 * 3 * comp
     if kind == "z_green":

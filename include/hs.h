@@ -70,10 +70,13 @@ typedef struct {
                            below inner_ratio times the FP64 residual's */
   int zchunk;           /* z planes per block of the x-pass (0 = automatic; a tiling knob that
                            does not change results beyond rounding order) */
+  int ytile;            /* y rows per block of the x-pass: 0 = automatic, or 2, 4, 8 dividing N2 */
+  int xfuse;            /* 0: x-direction FFTs in their own row passes around a real-space stencil
+                           pass (default); 1: one fused x-pass (inverse x FFT, stencil, forward x FFT) */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
- * inner_max 200, inner_ratio 1e-3, zchunk 0. */
+ * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0. */
 hs_status hs_default_options(hs_options* opt);
 
 /* Device workspace (bytes) that hs_create needs for this grid, precision and
@@ -131,14 +134,17 @@ hs_status hs_get_reference_medium(const hs_ctx* c, double C0[36]);
 
 /* Kernel classes reported by hs_profile_read. */
 enum {
-  HS_K_XPASS = 0,     /* fused x-pass: inverse x FFT, stencil, constitutive step, adjoint, forward x FFT */
+  HS_K_XPASS = 0,     /* real-space pass: stencil, constitutive step, adjoint stencil (with the x FFTs
+                         when xfuse = 1) */
   HS_K_YFWD = 1,      /* forward y FFT */
   HS_K_ZGREEN = 2,    /* forward z FFT, Green update, inverse z FFT */
   HS_K_YINV = 3,      /* inverse y FFT */
   HS_K_RESID64 = 4,   /* FP64 real-space residual sweep (HS_FP32_REFINED) */
   HS_K_FIELDS = 5,    /* output of eps and sigma */
   HS_K_OTHER = 6,     /* state transforms, correction accumulation, set-up */
-  HS_K_COUNT = 7
+  HS_K_XINV = 7,      /* inverse x FFT (half spectrum -> real rows), xfuse = 0 */
+  HS_K_XFWD = 8,      /* forward x FFT (real rows -> half spectrum), xfuse = 0 */
+  HS_K_COUNT = 9
 };
 
 /* Start (on != 0) or stop per-launch timing: every kernel launch of this context is then
@@ -149,7 +155,7 @@ hs_status hs_profile_enable(hs_ctx* c, int on);
 /* Accumulated device time (ms, from the events) and launch counts per kernel class since the
  * last read or enable; resets the accumulators.  ms and launches have HS_K_COUNT entries.
  * Launch counts are kept whether or not timing is enabled. */
-hs_status hs_profile_read(hs_ctx* c, double ms[7], long long launches[7]);
+hs_status hs_profile_read(hs_ctx* c, double ms[9], long long launches[9]);
 
 /* Limits of hs_residual_noalloc's fixed scratch array. */
 #define HS_NOALLOC_SCRATCH_BYTES (512 * 1024) /* bytes held on every device that loads the library */

@@ -22,7 +22,7 @@ thread_local std::string g_last_error;
 
 constexpr int kHistCap = 1 << 16;
 constexpr int kMaxN = 512;
-constexpr int kTargetBlocks = 608;  // 4 x 152 SMs
+constexpr int kTargetBlocks = 2048;  // x-pass blocks: ~13 per SM (z chunks of ~8 planes at 256^3)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -175,7 +175,7 @@ bool cholesky_pd(const double* A) {
 }
 
 struct Layout {
-  size_t S, B0, B1, ids, matk, matd, tw, partials, status, hist, u64, rsrc, total;
+  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, u64, rsrc, total;
 };
 
 }  // namespace
@@ -196,7 +196,8 @@ struct hs_ctx {
   size_t ws_bytes;
   Layout lay;
   void* S;
-  void* B[2];
+  void* B[2];  // xfuse: ping-pong spectral buffers; split: B[0] spectral work, B[1] real displacement
+  void* F;     // split: real force
   uint16_t* ids;
   void* matk;
   double* matd;
@@ -210,6 +211,9 @@ struct hs_ctx {
   int ty, zc, nthr_m;
   dim3 grid_m;
   int ct, nthr_y, nthr_z;
+  bool xfuse;
+  int nthr_row, nblk_row;
+  size_t smem_row;
   size_t smem_y, smem_z;
   dim3 grid_y, grid_z;
   bool warm;
@@ -290,15 +294,11 @@ int pitch_of(int nh, bool f64) { return f64 ? ((nh + 1) & ~1) : ((nh + 3) & ~3);
 
 int pick_ty(int n2) { return (n2 % 4 == 0) ? 4 : 2; }
 
-size_t march_smem(int n1, int ty, bool f64, int mode, bool real) {
-  const size_t cs = f64 ? 16 : 8, rs = f64 ? 8 : 4;
-  const int NR = ty + 2, NSI = 3 * NR / 2, NSF = 3 * ty / 2;
-  const int nthr = ((n1 + 31) / 32) * 32, nw = nthr / 32;
-  size_t ring = real ? 8 * 2 * 3 * NR * (size_t)n1 : cs * 2 * NSI * (size_t)n1;
-  size_t fbuf = (real || mode != hs::MODE_FORCE) ? 0 : cs * NSF * (size_t)n1;
-  size_t edge = ((real ? 8 : rs) * nw * (ty + 1) * 12 + 15) & ~size_t(15);
-  size_t red = 32 * hs::NRED * 8;
-  return ring + fbuf + edge + red;
+size_t march_smem(int n1, int ty, bool f64, int mode, bool real, bool has_src = false) {
+  const int nh = n1 / 2 + 1;
+  const int P = real ? 0 : pitch_of(nh, f64);
+  const int nthr = ((n1 + 31) / 32) * 32;
+  return hs::march_layout(n1, P, nthr, ty, mode, real, has_src, f64 ? 8 : 4).total;
 }
 
 Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
@@ -307,13 +307,13 @@ Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
   const int nh = n1 / 2 + 1, P = pitch_of(nh, f64);
   const size_t cs = f64 ? 16 : 8;
   const size_t N = (size_t)n1 * n2 * n3;
-  const size_t cbuf = align256((size_t)3 * n3 * n2 * P * cs);
-  const int ty = pick_ty(n2);
-  const size_t max_blocks = (size_t)(n2 / ty) * n3;  // upper bound over z-chunkings
+  const size_t cbuf = align256(std::max((size_t)3 * n3 * n2 * P * cs, 3 * N * (f64 ? 8 : 4)));
+  const size_t max_blocks = (size_t)(n2 / 2) * n3;  // upper bound over y tiles and z-chunkings
   size_t off = 0;
   L.S = off; off += cbuf;
   L.B0 = off; off += cbuf;
   L.B1 = off; off += cbuf;
+  L.F = off; off += cbuf;
   L.ids = off; off += align256(N * 2);
   L.matk = off; off += align256((size_t)nphase * 21 * (f64 ? 8 : 4));
   L.matd = off; off += align256((size_t)nphase * 21 * 8);
@@ -376,10 +376,59 @@ template <typename T> hs_status launch_force(hs_ctx* c, const double E[6], int i
   for (int i = 0; i < 6; ++i) a.E[i] = (T)E[i];
   a.src = src;
   a.skip_if_done = 1;
-  const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, hs::MODE_FORCE, false);
+  const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, hs::MODE_FORCE, false, src != nullptr);
   LaunchScope ls(c, HS_K_XPASS);
   cudaError_t e = hs::launch_march<T>(a, c->iso, c->ty, hs::MODE_FORCE, false, c->grid_m, c->nthr_m, sm, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(force)");
+  return HS_OK;
+}
+
+template <typename T> hs_status launch_rows(hs_ctx* c, int mode, double* acc64, bool skip) {
+  hs::RowArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  using C = typename hs::cplx_t<T>::type;
+  a.spec_in = (const C*)c->B[0];
+  a.spec_out = (C*)c->B[0];
+  a.real_in = (const T*)c->F;
+  a.real_out = acc64 ? nullptr : (T*)c->B[1];
+  a.acc64 = acc64;
+  a.tw = (const C*)c->twk[0];
+  a.plan = c->plan[0];
+  a.n1 = c->n1;
+  a.P = c->P;
+  a.nrows = 3 * c->n2 * c->n3;
+  a.st = c->st;
+  a.skip_if_done = skip ? 1 : 0;
+  cudaError_t e;
+  {
+    LaunchScope ls(c, acc64 ? HS_K_OTHER : (mode == hs::ROW_C2R ? HS_K_XINV : HS_K_XFWD));
+    e = hs::launch_row<T>(a, mode, c->nblk_row, c->nthr_row, c->smem_row, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_row");
+  return HS_OK;
+}
+
+// split x-pass: real-space stencil on the real displacement B[1], real force into F
+template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], const float* src, int mode, void* eps,
+                                               void* sig) {
+  hs::MarchArgs<T> a;
+  fill_march_common<T>(c, a);
+  a.ureal = (const T*)c->B[1];
+  for (int i = 0; i < 6; ++i) a.E[i] = (T)E[i];
+  a.src = src;
+  a.fout = c->F;
+  a.fout_f32 = 0;
+  a.eps_out = eps;
+  a.sig_out = sig;
+  a.out_f32 = c->opt.out_f32;
+  a.skip_if_done = (mode == hs::MODE_FORCE) ? 1 : 0;
+  const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, mode, true, src != nullptr);
+  cudaError_t e;
+  {
+    LaunchScope ls(c, mode == hs::MODE_FORCE ? HS_K_XPASS : HS_K_FIELDS);
+    e = hs::launch_march<T>(a, c->iso, c->ty, mode, true, c->grid_m, c->nthr_m, sm, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_march(real)");
   return HS_OK;
 }
 
@@ -476,17 +525,25 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
   const int chunk = std::max(1, c->opt.check_every);
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      hs_status s = launch_force<T>(c, E, cur, src);
-      if (s != HS_OK) return s;
-      s = launch_cols<T>(c, cur ^ 1);
-      if (s != HS_OK) return s;
-      cur ^= 1;
+      if (c->xfuse) {
+        hs_status s = launch_force<T>(c, E, cur, src);
+        if (s != HS_OK) return s;
+        s = launch_cols<T>(c, cur ^ 1);
+        if (s != HS_OK) return s;
+        cur ^= 1;
+      } else {
+        hs_status s = launch_rows<T>(c, hs::ROW_C2R, nullptr, true);
+        if (s == HS_OK) s = launch_stencil<T>(c, E, src, hs::MODE_FORCE, nullptr, nullptr);
+        if (s == HS_OK) s = launch_rows<T>(c, hs::ROW_R2C, nullptr, true);
+        if (s == HS_OK) s = launch_cols<T>(c, 0);
+        if (s != HS_OK) return s;
+      }
     }
     hs_status s = read_status(c, hst);
     if (s != HS_OK) return s;
     if (hst->done) break;
   }
-  *last_in = cur0 ^ ((hst->evals - 1) & 1);
+  *last_in = c->xfuse ? (cur0 ^ ((hst->evals - 1) & 1)) : 0;
   return HS_OK;
 }
 
@@ -515,7 +572,12 @@ hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, vo
   s = iterate<T>(c, E, nullptr, &h, &last_in);
   if (s != HS_OK) return s;
   if (eps != nullptr && sig != nullptr) {
-    s = launch_fields<T>(c, E, last_in, eps, sig);
+    if (c->xfuse) {
+      s = launch_fields<T>(c, E, last_in, eps, sig);
+    } else {
+      s = launch_rows<T>(c, hs::ROW_C2R, nullptr, false);
+      if (s == HS_OK) s = launch_stencil<T>(c, E, nullptr, hs::MODE_FIELDS, eps, sig);
+    }
     if (s != HS_OK) return s;
   }
   HS_CU(c, cudaStreamSynchronize(c->stream));
@@ -534,8 +596,9 @@ hs_status launch_residual64(hs_ctx* c, const double E[6], int mode, void* eps, v
   fill_march_common<double>(c, a);
   a.mat = c->matd;
   for (int i = 0; i < 6; ++i) a.E[i] = E[i];
-  a.u64 = c->u64;
+  a.ureal = c->u64;
   a.fout = c->rsrc;
+  a.fout_f32 = 1;
   a.eps_out = eps;
   a.sig_out = sig;
   a.out_f32 = c->opt.out_f32;
@@ -595,7 +658,7 @@ hs_status solve_refined(hs_ctx* c, const double E[6], double tol, int max_iter, 
     // u64 += du, du = inverse transform of the correction state
     s = launch_state_to_buf<float>(c, 0);
     if (s != HS_OK) return s;
-    s = launch_emit(c, 0);
+    s = c->xfuse ? launch_emit(c, 0) : launch_rows<float>(c, hs::ROW_C2R, c->u64, false);
     if (s != HS_OK) return s;
   }
   if (eps != nullptr && sig != nullptr) {
@@ -621,6 +684,8 @@ hs_status hs_default_options(hs_options* opt) {
   opt->inner_max = 200;
   opt->inner_ratio = 1e-3;
   opt->zchunk = 0;
+  opt->ytile = 0;
+  opt->xfuse = 0;
   return HS_OK;
 }
 
@@ -645,7 +710,9 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   hs_default_options(&o);
   if (opt) o = *opt;
   if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED || o.check_every < 1 || o.inner_max < 1 ||
-      !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0)
+      !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0 ||
+      !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
+      (o.xfuse != 0 && o.xfuse != 1))
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > 65536)
@@ -741,6 +808,7 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   c->S = c->ws + c->lay.S;
   c->B[0] = c->ws + c->lay.B0;
   c->B[1] = c->ws + c->lay.B1;
+  c->F = c->ws + c->lay.F;
   c->ids = (uint16_t*)(c->ws + c->lay.ids);
   c->matk = c->ws + c->lay.matk;
   c->matd = (double*)(c->ws + c->lay.matd);
@@ -756,7 +824,7 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   for (int ax = 0; ax < 3; ++ax) make_plan(grid[ax], &c->plan[ax]);
 
   // launch configuration
-  c->ty = pick_ty(c->n2);
+  c->ty = o.ytile > 0 ? o.ytile : pick_ty(c->n2);
   c->nthr_m = ((c->n1 + 31) / 32) * 32;
   const int ytiles = c->n2 / c->ty;
   int nzc = std::max(1, std::min(c->n3, (kTargetBlocks + ytiles - 1) / ytiles));
@@ -777,6 +845,15 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   const size_t cs = c->f64 ? 16 : 8;
   c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
   c->smem_z = (size_t)c->n3 * 3 * c->ct * cs;
+  c->xfuse = (o.xfuse == 1);
+  {
+    const int T8 = (c->n1 + hs::kE - 1) / hs::kE;
+    c->nthr_row = 256;
+    const int G = c->nthr_row / T8;
+    const size_t nseq = (size_t)3 * c->n2 * c->n3 / 2;
+    c->nblk_row = (int)std::min<size_t>((nseq + G - 1) / G, 65535);
+    c->smem_row = (size_t)G * hs::rpitch(c->n1) * cs;
+  }
   const int xtiles = (c->nh + c->ct - 1) / c->ct;
   c->grid_y = dim3(xtiles, c->n3);
   c->grid_z = dim3(xtiles, c->n2);
@@ -789,7 +866,9 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
     delete c;
     return st;
   }
-  const size_t need = std::max({march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, false),
+  const size_t need = std::max({c->xfuse ? march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, false, true)
+                                          : march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, true, true),
+                                c->smem_row,
                                 o.precision == HS_FP32_REFINED ? march_smem(c->n1, c->ty, true, hs::MODE_FORCE, true) : 0,
                                 c->smem_y, c->smem_z});
   if (need > (size_t)smem_optin) {

@@ -116,36 +116,62 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   const FftPlan plan = a.plan;
   const C* __restrict__ tw = a.tw;
   constexpr int W = 3 * CT;
-  for (int i = tid; i < L * W; i += nthr) {
-    const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;
-    sm[i] = (col < ncol) ? src[c * cstride + base + e * rstride + col] : cmk<C>(0, 0);
+  // tile load: 16-byte asynchronous copies; columns past the row pitch are zero
+  constexpr int EPC = 16 / (int)sizeof(C);  // complex values per 16-byte chunk
+  constexpr int CPR = CT / EPC;             // chunks per (row, component)
+  const int ccols = min(CT, a.P - x0);
+  for (int i = tid; i < L * 3 * CPR; i += nthr) {
+    const int e = i / (3 * CPR), rem = i - e * (3 * CPR), c = rem / CPR, col = (rem - c * CPR) * EPC;
+    C* dst = sm + e * W + c * CT + col;
+    if (col < ccols) {
+      cp_async16(dst, src + c * cstride + base + e * rstride + col);
+    } else {
+#pragma unroll
+      for (int q = 0; q < EPC; ++q) dst[q] = cmk<C>(0, 0);
+    }
   }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
-    HS_FFT(true, sm, 1, W, W, plan, tw, tid, nthr);
+    HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
   } else {
-    HS_FFT(false, sm, 1, W, W, plan, tw, tid, nthr);
+    HS_FFT_COLS(false, sm, W, W, plan, tw, tid, nthr);
   }
   if (MODE == COL_Z_GREEN) {
-    for (int i = tid; i < L * CT; i += nthr) {
-      const int z = i / CT, col = i - z * CT;
-      if (col >= ncol) continue;
-      C F[3], U[3];
-      const size_t g = base + z * rstride + col;
+    constexpr int GU = 4;  // points per thread per batch: state loads issued together
+    for (int i0 = tid; i0 < L * CT; i0 += GU * nthr) {
+      C U[GU][3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        F[c] = sm[z * W + c * CT + col];
-        U[c] = a.S[c * cstride + g];
+      for (int u = 0; u < GU; ++u) {
+        const int i = i0 + u * nthr;
+        const int z = i / CT, col = i - z * CT;
+        if (i < L * CT && col < ncol) {
+          const size_t g = base + z * rstride + col;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) U[u][c] = a.S[c * cstride + g];
+        }
       }
-      green_apply<T>(a, x0 + col, outer, z, F, U);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        a.S[c * cstride + g] = U[c];
-        sm[z * W + c * CT + col] = U[c];
+      for (int u = 0; u < GU; ++u) {
+        const int i = i0 + u * nthr;
+        const int z = i / CT, col = i - z * CT;
+        if (i < L * CT && col < ncol) {
+          C F[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) F[c] = sm[z * W + c * CT + col];
+          green_apply<T>(a, x0 + col, outer, z, F, U[u]);
+          const size_t g = base + z * rstride + col;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            a.S[c * cstride + g] = U[u][c];
+            sm[z * W + c * CT + col] = U[u][c];
+          }
+        }
       }
     }
     __syncthreads();
-    HS_FFT(true, sm, 1, W, W, plan, tw, tid, nthr);
+    HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
   }
   for (int i = tid; i < L * W; i += nthr) {
     const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;

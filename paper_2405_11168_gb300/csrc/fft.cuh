@@ -136,6 +136,14 @@ template <bool INV, typename C> struct Dft<16, INV, C> {
   static __device__ __forceinline__ void run(C* v) { dft_composite<4, 4, INV>(v); }
 };
 
+// 16-byte asynchronous global -> shared copies (cp.async, bypassing L1).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 constexpr int kMaxStages = 8;
 // Radix of each stage packed 4 bits per stage (stage 0 in the low bits), so
 // the plan is three plain integers and never needs indexed storage.
@@ -149,27 +157,34 @@ struct FftPlan {
 constexpr int kE = 8;
 
 template <int R, bool INV, typename C>
-__device__ __forceinline__ void stockham_stage(C* buf, int ss, int es, int s, int t, int T, bool active,
-                                               int L, int Ns, const C* __restrict__ tw) {
+__device__ __forceinline__ void stockham_stage(C* buf, int ss, int es, int ps, int s, int t, int T, bool active,
+                                               int L, int Ns, int nsh, const C* __restrict__ tw, bool wsync) {
+  // element e of sequence s lives at buf[s*ss + e*es + (ps >= 0 ? e >> ps : 0)]
+  // nsh >= 0: Ns = 2^nsh (shift/mask index math), else generic division
   constexpr int KB = (kE + R - 1) / R;
   C v[KB][R];
   const int nb = L / R;
+  const int step = L / (Ns * R);
+  C* sb = buf + s * ss;
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
     const int b = t + k * T;
     if (active && b < nb) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[k][m] = buf[s * ss + (b + m * nb) * es];
+      for (int m = 0; m < R; ++m) {
+        const int e = b + m * nb;
+        v[k][m] = sb[e * es + (ps >= 0 ? (e >> ps) : 0)];
+      }
     }
   }
-  __syncthreads();
+  if (wsync) __syncwarp(); else __syncthreads();
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
     const int b = t + k * T;
     if (active && b < nb) {
-      const int kk = b % Ns;
+      const int kk = (nsh >= 0) ? (b & (Ns - 1)) : (b % Ns);
+      const int pq = (nsh >= 0) ? (b >> nsh) : (b / Ns);
       if (Ns > 1) {
-        const int step = L / (Ns * R);
 #pragma unroll
         for (int m = 1; m < R; ++m) {
           C w = __ldg(tw + kk * m * step);
@@ -178,40 +193,59 @@ __device__ __forceinline__ void stockham_stage(C* buf, int ss, int es, int s, in
         }
       }
       Dft<R, INV, C>::run(v[k]);
-      const int base = (b / Ns) * Ns * R + kk;
+      const int base = pq * Ns * R + kk;
 #pragma unroll
-      for (int m = 0; m < R; ++m) buf[s * ss + (base + m * Ns) * es] = v[k][m];
+      for (int m = 0; m < R; ++m) {
+        const int e = base + m * Ns;
+        sb[e * es + (ps >= 0 ? (e >> ps) : 0)] = v[k][m];
+      }
     }
   }
-  __syncthreads();
+  if (wsync) __syncwarp(); else __syncthreads();
 }
 
 // FFT of nseq sequences in place.  All threads of the block must call this.
-// Thread i works on sequence (g0 + i / T) for each group start g0, where
-// T = ceil(L/kE) threads per sequence and (blockDim / T) sequences per group.
-template <bool INV, typename C>
-__device__ __forceinline__ void fft_smem(C* buf, int ss, int es, int nseq, int L, int nstage, int packed,
+// T = ceil(L/kE) threads per sequence, G = blockDim / T sequences per group.
+// COLMAP = false: thread i works on sequence g0 + i / T (lanes walk along one
+// sequence: for sequences stored as rows, element stride es = 1, padded with
+// ps = 3, i.e. one spare slot per 8 elements).  COLMAP = true: thread i works
+// on sequence g0 + i % G (lanes walk across sequences: for column tiles whose
+// sequences are adjacent in memory, ss = 1).  Either way a warp's shared-memory
+// accesses stay (nearly) free of bank conflicts.
+template <bool INV, bool COLMAP, typename C>
+__device__ __forceinline__ void fft_smem(C* buf, int ss, int es, int ps, int nseq, int L, int nstage, int packed,
                                          const C* __restrict__ tw, int tid, int nthreads) {
   const int T = (L + kE - 1) / kE;
   const int G = nthreads / T;
   for (int g0 = 0; g0 < nseq; g0 += G) {
-    const int s = g0 + tid / T;
-    const int t = tid % T;
-    const bool active = (tid / T) < G && s < nseq;
-    int Ns = 1;
+    const int sl = COLMAP ? (tid % G) : (tid / T);
+    const int t = COLMAP ? (tid / G) : (tid % T);
+    const int s = g0 + sl;
+    const bool active = (COLMAP ? (t < T) : (sl < G)) && s < nseq;
+    // row mapping with T dividing 32: every sequence lives inside one warp,
+    // so a warp barrier orders its stages (the caller syncs the block after)
+    const bool wsync = !COLMAP && T <= 32 && (32 % T) == 0 && (nthreads % 32) == 0;
+    int Ns = 1, nsh = 0;
 #pragma unroll 1
     for (int st = 0; st < nstage; ++st) {
       const int R = (packed >> (4 * st)) & 15;
-      if (R == 8) stockham_stage<8, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
-      else if (R == 4) stockham_stage<4, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
-      else if (R == 3) stockham_stage<3, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
-      else stockham_stage<2, INV>(buf, ss, es, s, t, T, active, L, Ns, tw);
+      if (R == 8) stockham_stage<8, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
+      else if (R == 4) stockham_stage<4, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
+      else if (R == 3) stockham_stage<3, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
+      else stockham_stage<2, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
       Ns *= R;
+      nsh = (nsh >= 0 && (R & (R - 1)) == 0) ? nsh + (R == 8 ? 3 : R == 4 ? 2 : 1) : -1;
     }
   }
 }
 
-#define HS_FFT(INV, buf, ss, es, nseq, plan, tw, tid, nthr) \
-  ::hs::fft_smem<INV>(buf, ss, es, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
+// padded index of element e in a row sequence (one spare slot per 8 elements)
+__host__ __device__ __forceinline__ int rpad(int e) { return e + (e >> 3); }
+__host__ __device__ __forceinline__ int rpitch(int n) { return n + (n >> 3) + 1; }
+
+#define HS_FFT_ROWS(INV, buf, pitch, nseq, plan, tw, tid, nthr)                                       \
+  ::hs::fft_smem<INV, false>(buf, pitch, 1, 3, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
+#define HS_FFT_COLS(INV, buf, W, nseq, plan, tw, tid, nthr) \
+  ::hs::fft_smem<INV, true>(buf, 1, W, -1, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
 
 }  // namespace hs

@@ -66,6 +66,15 @@ static cudaError_t col_ct(const ColArgs<T>& a, int mode, dim3 g, int nthr, size_
   }
 }
 
+template <typename T, int MODE>
+static cudaError_t row_one(const RowArgs<T>& a, int nb, int nthr, size_t smem, cudaStream_t s) {
+  auto k = k_row<T, MODE>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<nb, nthr, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_state_export(const typename cplx_t<T>::type* S, double2* out, size_t nrows, int nh, int P) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,10 +108,14 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
   template <>                                                                                            \
   cudaError_t launch_march<T>(const MarchArgs<T>& a, bool iso, int ty, int mode, bool real, dim3 grid,  \
                               int nthr, size_t smem, cudaStream_t s) {                                   \
-    if (real) {                                                                                          \
-      if (!(REALOK)) return cudaErrorInvalidValue;                                                       \
-      return march_real<T, REALOK>(a, iso, ty, mode, grid, nthr, smem, s);                               \
-    }                                                                                                    \
+    if (a.ids == nullptr || a.mat == nullptr || a.st == nullptr || a.partials == nullptr)                \
+      return cudaErrorInvalidValue;                                                                      \
+    if (real && a.ureal == nullptr) return cudaErrorInvalidValue;                                        \
+    if (!real && a.in == nullptr) return cudaErrorInvalidValue;                                          \
+    if (mode == MODE_EMIT && a.u64 == nullptr) return cudaErrorInvalidValue;                             \
+    if (mode == MODE_FORCE && !real && a.out == nullptr) return cudaErrorInvalidValue;                   \
+    if (mode == MODE_FIELDS && (a.eps_out == nullptr || a.sig_out == nullptr)) return cudaErrorInvalidValue; \
+    if (real) return march_real<T, true>(a, iso, ty, mode, grid, nthr, smem, s);                         \
     return march_real<T, false>(a, iso, ty, mode, grid, nthr, smem, s);                                  \
   }                                                                                                      \
   template <>                                                                                            \
@@ -110,6 +123,13 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
                             cudaStream_t s) {                                                            \
     if (ct != (CT)) return cudaErrorInvalidValue;                                                        \
     return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                                  \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_row<T>(const RowArgs<T>& a, int mode, int nb, int nthr, size_t smem, cudaStream_t s) { \
+    if (a.tw == nullptr || (mode == ROW_C2R ? (a.spec_in == nullptr || (a.real_out == nullptr && a.acc64 == nullptr)) \
+                                            : (a.real_in == nullptr || a.spec_out == nullptr)))         \
+      return cudaErrorInvalidValue;                                                                      \
+    return mode == ROW_C2R ? row_one<T, ROW_C2R>(a, nb, nthr, smem, s) : row_one<T, ROW_R2C>(a, nb, nthr, smem, s); \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t launch_state_export<T>(const typename cplx_t<T>::type* S, double2* out, int n2, int n3,     \

@@ -5,6 +5,7 @@
 
 #include "colpass.cuh"
 #include "march.cuh"
+#include "rowpass.cuh"
 
 namespace hs {
 
@@ -16,6 +17,10 @@ cudaError_t launch_march(const MarchArgs<T>& a, bool iso, int ty, int mode, bool
 
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
+
+// mode: ROW_C2R / ROW_R2C
+template <typename T>
+cudaError_t launch_row(const RowArgs<T>& a, int mode, int nblocks, int nthr, size_t smem, cudaStream_t s);
 
 // u8 phase ids -> u16
 cudaError_t launch_ids_u8_to_u16(const uint8_t* in, uint16_t* out, size_t n, cudaStream_t s);

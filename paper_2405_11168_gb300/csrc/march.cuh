@@ -47,8 +47,10 @@ template <typename T> struct MarchArgs {
   void* eps_out;         // FIELDS: [6][n3][n2][n1]
   void* sig_out;
   int out_f32;
-  double* u64;           // EMIT: += u ; REAL: input displacement [3][n3][n2][n1]
-  float* fout;           // REAL FORCE: real force [3][n3][n2][n1]
+  double* u64;           // EMIT: += u
+  const T* ureal;        // REAL: input displacement [3][n3][n2][n1]
+  void* fout;            // REAL FORCE: real force [3][n3][n2][n1], float if fout_f32 else T
+  int fout_f32;
   int skip_if_done;
 };
 
@@ -85,7 +87,6 @@ __device__ __forceinline__ void tetra_strains(const T (&u)[2][2][2][3], const T*
   e2[5] = E[5] + E[5] + g2[0][1] + g2[1][0];
 }
 
-// Corner plane zz (rows y0-1 .. y0+TY) into shared memory (see file comment).
 // Engineering strain of one tetrahedron (tt = 0: T1, tt = 1: T2).
 template <typename T>
 __device__ __forceinline__ void tetra_strain_one(const T (&u)[2][2][2][3], const T* E, int tt, T* e) {
@@ -114,58 +115,166 @@ __device__ __forceinline__ void tetra_strain_one(const T (&u)[2][2][2][3], const
   e[5] = E[5] + E[5] + g[0][1] + g[1][0];
 }
 
+// Shared-memory layout of k_march (host and device use the same function).
+struct MarchLayout {
+  size_t ring, fbuf, stage, ids, src, edge, red, total;
+  int n1i, n1s;  // row pitches (elements) of the ids and source stages
+};
+
+__host__ __device__ inline size_t hs_align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline MarchLayout march_layout(int n1, int P, int nthr, int ty, int mode, bool real,
+                                                    bool has_src, int tsize) {
+  MarchLayout L;
+  const int NR = ty + 2, NSI = 3 * NR / 2, NSF = 3 * ty / 2;
+  const size_t cs = 2 * (size_t)tsize;
+  L.n1i = (n1 + 7) & ~7;
+  L.n1s = (n1 + 3) & ~3;
+  size_t off = 0;
+  L.ring = off;
+  off += hs_align16(real ? (size_t)tsize * 3 * 3 * NR * n1 : cs * 2 * NSI * rpitch(n1));
+  L.fbuf = off;
+  off += hs_align16((real || mode != MODE_FORCE) ? 0 : cs * NSF * rpitch(n1));
+  L.stage = off;
+  off += hs_align16(real ? 0 : cs * 3 * NR * (size_t)P);
+  L.ids = off;
+  off += hs_align16(mode == MODE_EMIT ? 0 : (size_t)2 * 2 * (ty + 1) * L.n1i);
+  L.src = off;
+  off += hs_align16(has_src ? (size_t)4 * 2 * 3 * ty * L.n1s : 0);
+  L.edge = off;
+  off += hs_align16((size_t)tsize * (nthr / 32) * (ty + 1) * 12);
+  L.red = off;
+  off += 32 * NRED * 8;
+  L.total = off;
+  return L;
+}
+
+template <typename T> struct MarchPtrs {
+  const typename cplx_t<T>::type* in;
+  const T* ureal;
+  const uint16_t* ids;
+  const float* src;
+  typename cplx_t<T>::type* stage;
+  T* rring;
+  uint16_t* sids;
+  float* ssrc;
+  int n1, n2, n3, P, y0, n1i, n1s;
+};
+
+// Asynchronous prefetch of one plane's inputs: u rows of corner plane pu
+// (complex: into the staging rows; REAL: into ring slot rslot), ids rows of
+// voxel plane pu into ids buffer ib, source rows of output plane ps into
+// source buffer ib (ps < 0: none).  Ends with a commit of the copy group.
 template <typename T, int TY, bool REAL>
-__device__ __forceinline__ void march_load_plane(
-    typename cplx_t<T>::type* __restrict__ ring, T* __restrict__ rring, int slot, int zz,
-    const typename cplx_t<T>::type* __restrict__ in, const double* __restrict__ u64, int n1, int n2, int n3,
-    int P, int y0, const FftPlan& plan, const typename cplx_t<T>::type* __restrict__ tw1, int tid, int nthr) {
+__device__ __forceinline__ void march_prefetch(const MarchPtrs<T>& m, int tid, int nthr, int pu, int rslot, int ib,
+                                               int ps, bool want_ids) {
   using C = typename cplx_t<T>::type;
   constexpr int NR = TY + 2;
-  constexpr int NSI = 3 * NR / 2;
-  zz = ((zz % n3) + n3) % n3;
-  const size_t plane_stride = (size_t)n2 * P;
-  const size_t comp_stride = (size_t)n3 * plane_stride;
-  const size_t rplane = (size_t)n2 * n1;
-  const size_t rcomp = (size_t)n3 * rplane;
+  constexpr int EPC = 16 / (int)sizeof(C);
+  const int n1 = m.n1, n2 = m.n2, n3 = m.n3, P = m.P, y0 = m.y0;
+  const size_t rplane = (size_t)n2 * n1, rcomp = (size_t)n3 * rplane;
+  const size_t plane_stride = (size_t)n2 * P, comp_stride = (size_t)n3 * plane_stride;
+  const int gz = ((pu % n3) + n3) % n3;
   if (REAL) {
-    for (int i = tid; i < 3 * NR * n1; i += nthr) {
-      const int r = i / n1, k = i - r * n1;
-      const int c = r / NR, j = r - c * NR;
-      const int yy = (y0 - 1 + j + n2) % n2;
-      rring[slot * 3 * NR * n1 + i] = (T)u64[c * rcomp + (size_t)zz * rplane + (size_t)yy * n1 + k];
+    constexpr int EPR = 16 / (int)sizeof(T);  // real values per 16-byte chunk
+    T* dst0 = m.rring + (size_t)rslot * 3 * NR * n1;
+    if (n1 % EPR == 0) {
+      const int nch = n1 / EPR;
+      for (int i = tid; i < 3 * NR * nch; i += nthr) {
+        const int r = i / nch, ch = i - r * nch;
+        const int c = r / NR, j = r - c * NR;
+        const int gy = (y0 - 1 + j + n2) % n2;
+        cp_async16(dst0 + (size_t)r * n1 + EPR * ch,
+                   m.ureal + c * rcomp + (size_t)gz * rplane + (size_t)gy * n1 + EPR * ch);
+      }
+    } else if (tid < n1) {
+      for (int r = 0; r < 3 * NR; ++r) {
+        const int c = r / NR, j = r - c * NR;
+        const int gy = (y0 - 1 + j + n2) % n2;
+        dst0[(size_t)r * n1 + tid] = m.ureal[c * rcomp + (size_t)gz * rplane + (size_t)gy * n1 + tid];
+      }
     }
-    __syncthreads();
   } else {
-    C* R = ring + slot * NSI * n1;
-    const int half = n1 / 2;
-    for (int i = tid; i < NSI * n1; i += nthr) {
-      const int q = i / n1, k = i - q * n1;
-      const int ra = 2 * q;
-      const int c = ra / NR, ja = ra - c * NR;
-      const int ya = (y0 - 1 + ja + n2) % n2, yb = (y0 + ja + n2) % n2;
-      const int kk = (k <= half) ? k : n1 - k;
-      const size_t base = c * comp_stride + (size_t)zz * plane_stride + kk;
-      C A = in[base + (size_t)ya * P];
-      C B = in[base + (size_t)yb * P];
+    const int nh = n1 / 2 + 1;
+    const int nch = (nh + EPC - 1) / EPC;
+    for (int i = tid; i < 3 * NR * nch; i += nthr) {
+      const int r = i / nch, ch = i - r * nch;
+      const int c = r / NR, j = r - c * NR;
+      const int gy = (y0 - 1 + j + n2) % n2;
+      cp_async16(m.stage + (size_t)r * P + ch * EPC,
+                 m.in + c * comp_stride + (size_t)gz * plane_stride + (size_t)gy * P + ch * EPC);
+    }
+  }
+  if (want_ids) {
+    uint16_t* d = m.sids + (size_t)ib * (TY + 1) * m.n1i;
+    if ((n1 & 7) == 0) {
+      const int nch = n1 / 8;
+      for (int i = tid; i < (TY + 1) * nch; i += nthr) {
+        const int r = i / nch, ch = i - r * nch;
+        const int gy = (y0 + r) % n2;
+        cp_async16(d + (size_t)r * m.n1i + 8 * ch, m.ids + ((size_t)gz * n2 + gy) * n1 + 8 * ch);
+      }
+    } else if (tid < n1) {
+      for (int r = 0; r <= TY; ++r) d[(size_t)r * m.n1i + tid] = m.ids[((size_t)gz * n2 + (y0 + r) % n2) * n1 + tid];
+    }
+  }
+  if (m.src != nullptr && ps >= 0) {
+    float* d = m.ssrc + (size_t)ib * 3 * TY * m.n1s;
+    const int zs = ps % n3;
+    if ((n1 & 3) == 0) {
+      const int nch = n1 / 4;
+      for (int i = tid; i < 3 * TY * nch; i += nthr) {
+        const int r = i / nch, ch = i - r * nch;
+        const int c = r / TY, rr = r - c * TY;
+        cp_async16(d + (size_t)r * m.n1s + 4 * ch, m.src + c * rcomp + (size_t)zs * rplane + (size_t)(y0 + rr) * n1 + 4 * ch);
+      }
+    } else if (tid < n1) {
+      for (int r = 0; r < 3 * TY; ++r) {
+        const int c = r / TY, rr = r - c * TY;
+        d[(size_t)r * m.n1s + tid] = m.src[c * rcomp + (size_t)zs * rplane + (size_t)(y0 + rr) * n1 + tid];
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+// Staged raw rows -> packed complex sequences of ring slot `slot` (two real
+// rows per sequence: Z = A + iB with the Hermitian extension of the half
+// spectra; imaginary parts of the k = 0 and k = N1/2 bins dropped).
+template <typename T, int TY>
+__device__ __forceinline__ void march_pack(const MarchPtrs<T>& m, typename cplx_t<T>::type* ring, int x, bool xact,
+                                           int slot) {
+  using C = typename cplx_t<T>::type;
+  constexpr int NSI = 3 * (TY + 2) / 2;
+  const int n1 = m.n1, P = m.P;
+  const int n1p = rpitch(n1);
+  C* R = ring + slot * NSI * n1p;
+  const int half = n1 / 2;
+  if (xact) {
+    const int k = x;
+    const int kk = (k <= half) ? k : n1 - k;
+#pragma unroll
+    for (int q = 0; q < NSI; ++q) {
+      C A = m.stage[(size_t)(2 * q) * P + kk];
+      C B = m.stage[(size_t)(2 * q + 1) * P + kk];
       if (kk == 0 || kk == half) { A.y = 0; B.y = 0; }
       C Z;
       if (k <= half) { Z.x = A.x - B.y; Z.y = A.y + B.x; }
       else { Z.x = A.x + B.y; Z.y = B.x - A.y; }
-      R[i] = Z;
+      R[q * n1p + rpad(k)] = Z;
     }
-    __syncthreads();
-    HS_FFT(true, R, n1, 1, NSI, plan, tw1, tid, nthr);
   }
+  __syncthreads();
 }
 
 template <typename T, int TY, bool REAL>
-__device__ __forceinline__ T march_u(const typename cplx_t<T>::type* __restrict__ ring,
-                                     const T* __restrict__ rring, int slot, int c, int j, int xx, int n1) {
+__device__ __forceinline__ T march_u(const typename cplx_t<T>::type* ring, const T* rring, int n1, int slot, int c,
+                                     int j, int xx) {
   constexpr int NR = TY + 2;
   constexpr int NSI = 3 * NR / 2;
-  if (REAL) return rring[((slot * 3 + c) * NR + j) * n1 + xx];
+  if (REAL) return rring[((size_t)slot * 3 * NR + c * NR + j) * n1 + xx];
   const int r = c * NR + j;
-  const auto z = ring[(slot * NSI + (r >> 1)) * n1 + xx];
+  const auto z = ring[(slot * NSI + (r >> 1)) * rpitch(n1) + rpad(xx)];
   return (r & 1) ? z.y : z.x;
 }
 
@@ -175,11 +284,11 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
   constexpr int NR = TY + 2;          // corner rows per plane (1 halo row each side)
   constexpr int NSI = 3 * NR / 2;     // packed complex sequences per plane
   constexpr int NSF = 3 * TY / 2;     // packed sequences of the output force
+  constexpr int EPC = 16 / (int)sizeof(C);
   if (a.skip_if_done && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3, P = a.P, nh = n1 / 2 + 1;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = nthr >> 5;
   const int y0 = blockIdx.x * TY;
   const int z0 = blockIdx.y * a.zc;
   const int zc = min(a.zc, n3 - z0);
@@ -192,36 +301,60 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
   const uint16_t* __restrict__ ids = a.ids;
   const C* __restrict__ tw1 = a.tw1;
   const FftPlan plan = a.plan1;
+  const bool has_src = (a.src != nullptr);
 
-  // shared memory carve
-  C* ring = reinterpret_cast<C*>(smraw);                           // [2][NSI][n1] (complex path)
-  T* rring = reinterpret_cast<T*>(smraw);                          // [2][3][NR][n1] (REAL path)
-  const size_t ring_bytes = REAL ? sizeof(T) * 2 * 3 * NR * n1 : sizeof(C) * 2 * NSI * n1;
-  C* fbuf = reinterpret_cast<C*>(smraw + ring_bytes);              // [NSF][n1]
-  const size_t fbuf_bytes = (REAL || MODE != MODE_FORCE) ? 0 : sizeof(C) * NSF * n1;
-  T* edge = reinterpret_cast<T*>(smraw + ring_bytes + fbuf_bytes); // [nwarps][TY+1][12]
-  double* red = reinterpret_cast<double*>(smraw + ring_bytes + fbuf_bytes +
-                                          ((sizeof(T) * nwarps * (TY + 1) * 12 + 15) & ~size_t(15)));
+  const MarchLayout lay = march_layout(n1, P, nthr, TY, MODE, REAL, has_src, (int)sizeof(T));
+  C* ring = reinterpret_cast<C*>(smraw + lay.ring);      // complex: [2][NSI][n1]
+  T* rring = reinterpret_cast<T*>(smraw + lay.ring);     // REAL: [3][3*NR][n1]
+  C* fbuf = reinterpret_cast<C*>(smraw + lay.fbuf);      // [NSF][n1]
+  C* stage = reinterpret_cast<C*>(smraw + lay.stage);    // [3*NR][P] raw rows of the next plane
+  uint16_t* sids = reinterpret_cast<uint16_t*>(smraw + lay.ids);  // [2][TY+1][n1i]
+  float* ssrc = reinterpret_cast<float*>(smraw + lay.src);        // [2][3*TY][n1s]
+  T* edge = reinterpret_cast<T*>(smraw + lay.edge);      // [nwarps][TY+1][12]
+  double* red = reinterpret_cast<double*>(smraw + lay.red);
 
   const int x = tid;
   const bool xact = x < n1;
   const int xm = (x == 0) ? n1 - 1 : x - 1;
   const int xr = xact ? x : 0, xmr = xact ? xm : 0;
 
+  MarchPtrs<T> mp;
+  mp.in = in;
+  mp.ureal = a.ureal;
+  mp.ids = ids;
+  mp.src = a.src;
+  mp.stage = stage;
+  mp.rring = rring;
+  mp.sids = sids;
+  mp.ssrc = ssrc;
+  mp.n1 = n1;
+  mp.n2 = n2;
+  mp.n3 = n3;
+  mp.P = P;
+  mp.y0 = y0;
+  mp.n1i = lay.n1i;
+  mp.n1s = lay.n1s;
+
   if (MODE == MODE_EMIT) {
     double* __restrict__ u64 = a.u64;
+    march_prefetch<T, TY, REAL>(mp, tid, nthr, z0, 0, 0, -1, false);
     for (int p = z0; p < z0 + zc; ++p) {
-      march_load_plane<T, TY, false>(ring, rring, 0, p, in, nullptr, n1, n2, n3, P, y0, plan, tw1, tid, nthr);
+      cp_async_wait_all();
+      __syncthreads();
+      march_pack<T, TY>(mp, ring, x, xact, 0);
+      if (p + 1 < z0 + zc) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, 0, 0, -1, false);
+      HS_FFT_ROWS(true, ring, rpitch(n1), NSI, plan, tw1, tid, nthr);
+      __syncthreads();
       if (xact) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int r = 0; r < TY; ++r)
-            u64[c * rcomp + (size_t)p * rplane + (size_t)(y0 + r) * n1 + x] +=
-                (double)march_u<T, TY, false>(ring, rring, 0, c, r + 1, x, n1);
+            u64[c * rcomp + (size_t)p * rplane + (size_t)(y0 + r) * n1 + x] += (double)march_u<T, TY, REAL>(ring, rring, n1, 0, c, r + 1, x);
       }
       __syncthreads();
     }
+    cp_async_wait_all();
     return;
   }
 
@@ -242,22 +375,49 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
   const bool recv_edge = xact && !recv_shfl;
   const int src_warp = ((x + 1) % n1) >> 5;
 
-  march_load_plane<T, TY, REAL>(ring, rring, 0, z0 - 1, in, a.u64, n1, n2, n3, P, y0, plan, tw1, tid, nthr);
+  // prologue: plane z0-1, then the prefetch of plane z0
+  if (REAL) {
+    march_prefetch<T, TY, REAL>(mp, tid, nthr, z0 - 1, 0, 0, -1, false);
+    march_prefetch<T, TY, REAL>(mp, tid, nthr, z0, 1, 0, -1, true);
+  } else {
+    march_prefetch<T, TY, REAL>(mp, tid, nthr, z0 - 1, 0, 0, -1, false);
+    cp_async_wait_all();
+    __syncthreads();
+    march_pack<T, TY>(mp, ring, x, xact, 0);
+    march_prefetch<T, TY, REAL>(mp, tid, nthr, z0, 0, 0, -1, true);
+    HS_FFT_ROWS(true, ring, rpitch(n1), NSI, plan, tw1, tid, nthr);
+    __syncthreads();
+  }
   const int pend = (MODE == MODE_FORCE) ? z0 + zc : z0 + zc - 1;
   for (int p = z0; p <= pend; ++p) {
-    const int sc = (p - z0 + 1) & 1, sp = sc ^ 1;
-    march_load_plane<T, TY, REAL>(ring, rring, sc, p, in, a.u64, n1, n2, n3, P, y0, plan, tw1, tid, nthr);
+    const int ib = (p - z0) & 1;  // ids buffer of voxel plane p, source buffer of output plane p-1
+    int sc, sp;
+    cp_async_wait_all();
+    __syncthreads();
+    if (REAL) {
+      sc = (p - z0 + 1) % 3;
+      sp = (p - z0) % 3;
+      if (p < pend) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, (p - z0 + 2) % 3, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
+    } else {
+      sc = (p - z0 + 1) & 1;
+      sp = sc ^ 1;
+      march_pack<T, TY>(mp, ring, x, xact, sc);
+      if (p < pend) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, 0, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
+      HS_FFT_ROWS(true, ring + sc * NSI * rpitch(n1), rpitch(n1), NSI, plan, tw1, tid, nthr);
+      __syncthreads();
+    }
     const int pz = p % n3;
     const bool own_plane = p < z0 + zc;
+    const uint16_t* idrow = sids + (size_t)ib * (TY + 1) * lay.n1i;
 
     // ---- per-voxel work: rows jj = 1..TY+1 (voxel y = y0 + jj - 1) ----
     T uc[2][3][2];  // cached corner values of row jj: [ox][comp][oz]
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      uc[0][c][0] = march_u<T, TY, REAL>(ring, rring, sc, c, 0, xr, n1);
-      uc[0][c][1] = march_u<T, TY, REAL>(ring, rring, sp, c, 0, xr, n1);
-      uc[1][c][0] = march_u<T, TY, REAL>(ring, rring, sc, c, 0, xmr, n1);
-      uc[1][c][1] = march_u<T, TY, REAL>(ring, rring, sp, c, 0, xmr, n1);
+      uc[0][c][0] = march_u<T, TY, REAL>(ring, rring, n1, sc, c, 0, xr);
+      uc[0][c][1] = march_u<T, TY, REAL>(ring, rring, n1, sp, c, 0, xr);
+      uc[1][c][0] = march_u<T, TY, REAL>(ring, rring, n1, sc, c, 0, xmr);
+      uc[1][c][1] = march_u<T, TY, REAL>(ring, rring, n1, sp, c, 0, xmr);
     }
 #pragma unroll
     for (int jj = 1; jj <= TY + 1; ++jj) {
@@ -270,15 +430,15 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
           u[ox][1][0][c] = uc[ox][c][0];
           u[ox][1][1][c] = uc[ox][c][1];
         }
-        const T v00 = march_u<T, TY, REAL>(ring, rring, sc, c, jj, xr, n1);
-        const T v01 = march_u<T, TY, REAL>(ring, rring, sp, c, jj, xr, n1);
-        const T v10 = march_u<T, TY, REAL>(ring, rring, sc, c, jj, xmr, n1);
-        const T v11 = march_u<T, TY, REAL>(ring, rring, sp, c, jj, xmr, n1);
+        const T v00 = march_u<T, TY, REAL>(ring, rring, n1, sc, c, jj, xr);
+        const T v01 = march_u<T, TY, REAL>(ring, rring, n1, sp, c, jj, xr);
+        const T v10 = march_u<T, TY, REAL>(ring, rring, n1, sc, c, jj, xmr);
+        const T v11 = march_u<T, TY, REAL>(ring, rring, n1, sp, c, jj, xmr);
         u[0][0][0][c] = v00; u[0][0][1][c] = v01; u[1][0][0][c] = v10; u[1][0][1][c] = v11;
         uc[0][c][0] = v00; uc[0][c][1] = v01; uc[1][c][0] = v10; uc[1][c][1] = v11;
       }
       const int yv = (y0 + jj - 1) % n2;
-      const int ph = __ldg(ids + ((size_t)pz * n2 + yv) * n1 + xr);
+      const int ph = idrow[(size_t)(jj - 1) * lay.n1i + xr];
       if (MODE == MODE_FIELDS) {
         T e1[6], e2[6], s1[6], s2[6];
         tetra_strains(u, E, e1, e2);
@@ -354,10 +514,7 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
         }
       }
     }
-    if (MODE == MODE_FIELDS) {
-      __syncthreads();
-      continue;
-    }
+    if (MODE == MODE_FIELDS) continue;
     __syncthreads();
     if (recv_edge) {
 #pragma unroll
@@ -374,12 +531,12 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
     if (p > z0) {
       // corner plane p-1 is complete
       const int zp = (p - 1) % n3;
-      if (a.src != nullptr && xact) {
+      if (has_src && xact) {
+        const float* sr = ssrc + (size_t)ib * 3 * TY * lay.n1s;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int r = 0; r < TY; ++r)
-            Fp[r][c] += (T)a.src[c * rcomp + (size_t)zp * rplane + (size_t)(y0 + r) * n1 + x];
+          for (int r = 0; r < TY; ++r) Fp[r][c] += (T)sr[(size_t)(c * TY + r) * lay.n1s + x];
       }
       if (xact) {
 #pragma unroll
@@ -392,8 +549,11 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int r = 0; r < TY; ++r)
-              a.fout[c * rcomp + (size_t)zp * rplane + (size_t)(y0 + r) * n1 + x] = (float)Fp[r][c];
+            for (int r = 0; r < TY; ++r) {
+              const size_t o = c * rcomp + (size_t)zp * rplane + (size_t)(y0 + r) * n1 + x;
+              if (a.fout_f32) reinterpret_cast<float*>(a.fout)[o] = (float)Fp[r][c];
+              else reinterpret_cast<T*>(a.fout)[o] = Fp[r][c];
+            }
         }
       } else {
         if (xact) {
@@ -404,25 +564,29 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
               C z;
               z.x = Fp[r][c];
               z.y = Fp[r + 1][c];
-              fbuf[((c * TY + r) >> 1) * n1 + x] = z;
+              fbuf[((c * TY + r) >> 1) * rpitch(n1) + rpad(x)] = z;
             }
         }
         __syncthreads();
-        HS_FFT(false, fbuf, n1, 1, NSF, plan, tw1, tid, nthr);
-        for (int i = tid; i < NSF * nh; i += nthr) {
-          const int q = i / nh, k = i - q * nh;
-          const C Zk = fbuf[q * n1 + k];
-          const C Zn = fbuf[q * n1 + (k == 0 ? 0 : n1 - k)];
-          C A, B;
-          A.x = T(0.5) * (Zk.x + Zn.x);
-          A.y = T(0.5) * (Zk.y - Zn.y);
-          B.x = T(0.5) * (Zk.y + Zn.y);
-          B.y = T(0.5) * (Zn.x - Zk.x);
-          const int ra = 2 * q;
-          const int c = ra / TY, r = ra - c * TY;
-          const size_t o = c * comp_stride + (size_t)zp * plane_stride + (size_t)(y0 + r) * P + k;
-          out[o] = A;
-          out[o + P] = B;
+        HS_FFT_ROWS(false, fbuf, rpitch(n1), NSF, plan, tw1, tid, nthr);
+        __syncthreads();
+        if (x < nh) {
+          const int k = x;
+#pragma unroll
+          for (int q = 0; q < NSF; ++q) {
+            const C Zk = fbuf[q * rpitch(n1) + rpad(k)];
+            const C Zn = fbuf[q * rpitch(n1) + rpad(k == 0 ? 0 : n1 - k)];
+            C A, B;
+            A.x = T(0.5) * (Zk.x + Zn.x);
+            A.y = T(0.5) * (Zk.y - Zn.y);
+            B.x = T(0.5) * (Zk.y + Zn.y);
+            B.y = T(0.5) * (Zn.x - Zk.x);
+            const int ra = 2 * q;
+            const int c = ra / TY, r = ra - c * TY;
+            const size_t o = c * comp_stride + (size_t)zp * plane_stride + (size_t)(y0 + r) * P + k;
+            out[o] = A;
+            out[o + P] = B;
+          }
         }
       }
     }
@@ -431,6 +595,7 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
 #pragma unroll
       for (int k = 0; k < 3; ++k) { Fp[r][k] = Fn[r][k]; Fn[r][k] = 0; }
   }
+  cp_async_wait_all();
   if (MODE != MODE_FORCE) return;
   double acc[NRED];
 #pragma unroll

@@ -157,12 +157,11 @@ extern "C" hs_status hs_residual_noalloc(const int grid[3], const unsigned short
   a.partials = partials;
   a.st = st;
   a.hist = hist;
-  a.u64 = const_cast<double*>(u);
+  a.ureal = u;
   a.fout = force;
+  a.fout_f32 = 1;
   a.skip_if_done = 0;
-  const int NR = ty + 2;
-  const size_t smem = 8 * 2 * 3 * (size_t)NR * n1 + ((8 * (nthr / 32) * (ty + 1) * 12 + 15) & ~size_t(15)) +
-                      32 * hs::NRED * 8;
+  const size_t smem = hs::march_layout(n1, 0, nthr, ty, hs::MODE_FORCE, true, false, 8).total;
   e = hs::launch_march<double>(a, iso, ty, hs::MODE_FORCE, true, dim3(ytiles, nzc), nthr, smem, s);
   if (e != cudaSuccess) return HS_ERR_CUDA;
   e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);

@@ -28,7 +28,7 @@ HS_DIVERGED = -5
 HS_ERR_TIMEOUT = -6
 
 HS_FP64, HS_FP32, HS_FP32_REFINED = 0, 1, 2
-KERNEL_CLASSES = ["xpass", "y_fwd", "z_green", "y_inv", "resid64", "fields", "other"]
+KERNEL_CLASSES = ["xpass", "y_fwd", "z_green", "y_inv", "resid64", "fields", "other", "x_inv", "x_fwd"]
 HS_IDS_U8, HS_IDS_U16 = 0, 1
 
 # every exported function of include/hs.h
@@ -57,7 +57,8 @@ class hs_material(ctypes.Structure):
 
 class hs_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("out_f32", ctypes.c_int),
-                ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double), ("zchunk", ctypes.c_int)]
+                ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double), ("zchunk", ctypes.c_int),
+                ("ytile", ctypes.c_int), ("xfuse", ctypes.c_int)]
 
 
 class HSError(RuntimeError):
@@ -226,8 +227,8 @@ class Solver:
 
     def profile_read(self):
         """{class: (ms, launches)} since the last read."""
-        ms = np.zeros(7)
-        n = (ctypes.c_longlong * 7)()
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = (ctypes.c_longlong * len(KERNEL_CLASSES))()
         _check(self.lib, self.lib.hs_profile_read(self.ctx, _dp(ms), n), self.ctx)
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
