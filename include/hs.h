@@ -73,10 +73,13 @@ typedef struct {
   int ytile;            /* y rows per block of the x-pass: 0 = automatic, or 2, 4, 8 dividing N2 */
   int xfuse;            /* 0: x-direction FFTs in their own row passes around a real-space stencil
                            pass (default); 1: one fused x-pass (inverse x FFT, stencil, forward x FFT) */
+  int col_tile;         /* y/z FFT tile width in complex columns: 0 = automatic; FP32 8 or 16, FP64 4 or 8 */
+  int col_threads;      /* threads per y/z FFT block: 0 = automatic; a multiple of 32, at most 768 (FP32)
+                           or 384 (FP64) */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
- * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0. */
+ * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0, col_tile 0, col_threads 0. */
 hs_status hs_default_options(hs_options* opt);
 
 /* Device workspace (bytes) that hs_create needs for this grid, precision and

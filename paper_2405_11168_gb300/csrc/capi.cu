@@ -686,6 +686,8 @@ hs_status hs_default_options(hs_options* opt) {
   opt->zchunk = 0;
   opt->ytile = 0;
   opt->xfuse = 0;
+  opt->col_tile = 0;
+  opt->col_threads = 0;
   return HS_OK;
 }
 
@@ -712,7 +714,7 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED || o.check_every < 1 || o.inner_max < 1 ||
       !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0 ||
       !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
-      (o.xfuse != 0 && o.xfuse != 1))
+      (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0)
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > 65536)
@@ -832,13 +834,29 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   if (o.zchunk > 0) c->zc = std::min(o.zchunk, c->n3);
   nzc = (c->n3 + c->zc - 1) / c->zc;
   c->grid_m = dim3(ytiles, nzc);
-  c->ct = c->f64 ? 8 : 16;
+  // measured on GB300 at 256^3: narrow tiles in small blocks overlap best
+  c->ct = c->f64 ? 4 : 8;
+  if (o.col_tile > 0) {
+    if (o.col_tile != (c->f64 ? 8 : 16) && o.col_tile != (c->f64 ? 4 : 8)) {
+      delete c;
+      return fail(nullptr, HS_ERR_INVALID_ARG, "col_tile must be 8 or 16 (FP32), 4 or 8 (FP64)");
+    }
+    c->ct = o.col_tile;
+  }
   const int maxthr = c->f64 ? 384 : 768;
+  if (o.col_threads > maxthr) {
+    delete c;
+    return fail(nullptr, HS_ERR_INVALID_ARG, "col_threads above the block limit");
+  }
   auto col_threads = [&](int L) {
     const int T = (L + hs::kE - 1) / hs::kE;
     int n = 3 * c->ct * T;
     n = ((n + 31) / 32) * 32;
-    return std::min(n, (maxthr / T) * T);
+    n = std::min(n, (maxthr / T) * T);
+    const int dflt = c->f64 ? 128 : 256;
+    n = std::min(n, std::max(T, (dflt / T) * T));
+    if (o.col_threads > 0) n = std::max(T, (o.col_threads / T) * T);
+    return n;
   };
   c->nthr_y = col_threads(c->n2);
   c->nthr_z = col_threads(c->n3);

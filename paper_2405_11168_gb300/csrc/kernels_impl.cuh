@@ -121,8 +121,11 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
   template <>                                                                                            \
   cudaError_t launch_col<T>(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem,      \
                             cudaStream_t s) {                                                            \
-    if (ct != (CT)) return cudaErrorInvalidValue;                                                        \
-    return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                                  \
+    if (a.buf == nullptr || a.tw == nullptr || ((mode == COL_Z_GREEN || mode == COL_Z_INV_STATE) && a.S == nullptr)) \
+      return cudaErrorInvalidValue;                                                                      \
+    if (ct == (CT)) return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                  \
+    if (ct == (CT) / 2) return col_ct<T, (CT) / 2>(a, mode, grid, nthr, smem, s);                        \
+    return cudaErrorInvalidValue;                                                                        \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t launch_row<T>(const RowArgs<T>& a, int mode, int nb, int nthr, size_t smem, cudaStream_t s) { \

@@ -37,7 +37,7 @@ __device__ __forceinline__ void group_sync(bool wsync) {
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
+__global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
   using C = typename cplx_t<T>::type;
   if (a.skip_if_done && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
       if (act) {
         const C* A = a.spec_in + r0 * P;
         const C* B = a.spec_in + r1 * P;
+#pragma unroll 4
         for (int k = t; k < n1; k += T8) {
           const int kk = (k <= half) ? k : n1 - k;
           C va = A[kk], vb = B[kk];
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
       if (act) {
         const T* ra = a.real_in + r0 * n1;
         const T* rb = a.real_in + r1 * n1;
+#pragma unroll 4
         for (int x = t; x < n1; x += T8) {
           C w;
           w.x = ra[x];
