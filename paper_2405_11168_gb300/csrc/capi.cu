@@ -210,6 +210,9 @@ struct hs_ctx {
   FftPlan plan[3];
   int ty, zc, nthr_m;
   dim3 grid_m;
+  int ty64;       // y rows per block of the FP64 residual sweep (refined mode)
+  int zc64;
+  dim3 grid_m64;
   int ct, nthr_y, nthr_z;
   bool xfuse;
   int nthr_row, nblk_row;
@@ -599,13 +602,14 @@ hs_status launch_residual64(hs_ctx* c, const double E[6], int mode, void* eps, v
   a.ureal = c->u64;
   a.fout = c->rsrc;
   a.fout_f32 = 1;
+  a.zc = c->zc64;
   a.eps_out = eps;
   a.sig_out = sig;
   a.out_f32 = c->opt.out_f32;
   a.skip_if_done = 0;
-  const size_t sm = march_smem(c->n1, c->ty, true, mode, true);
+  const size_t sm = march_smem(c->n1, c->ty64, true, mode, true);
   LaunchScope ls(c, mode == hs::MODE_FORCE ? HS_K_RESID64 : HS_K_FIELDS);
-  cudaError_t e = hs::launch_march<double>(a, c->iso, c->ty, mode, true, c->grid_m, c->nthr_m, sm, c->stream);
+  cudaError_t e = hs::launch_march<double>(a, c->iso, c->ty64, mode, true, c->grid_m64, c->nthr_m, sm, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(residual fp64)");
   return HS_OK;
 }
@@ -884,10 +888,23 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
     delete c;
     return st;
   }
+  // FP64 residual sweep: the widest row tile whose plane ring fits
+  c->ty64 = c->ty;
+  if (o.precision == HS_FP32_REFINED) {
+    while (c->ty64 > 2 && march_smem(c->n1, c->ty64, true, hs::MODE_FORCE, true) > (size_t)smem_optin) c->ty64 /= 2;
+    if (c->n2 % c->ty64 != 0) c->ty64 = 2;
+  }
+  {
+    const int yt = c->n2 / c->ty64;
+    int nz = std::max(1, std::min(c->n3, (kTargetBlocks + yt - 1) / yt));
+    c->zc64 = (c->n3 + nz - 1) / nz;
+    nz = (c->n3 + c->zc64 - 1) / c->zc64;
+    c->grid_m64 = dim3(yt, nz);
+  }
   const size_t need = std::max({c->xfuse ? march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, false, true)
                                           : march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, true, true),
                                 c->smem_row,
-                                o.precision == HS_FP32_REFINED ? march_smem(c->n1, c->ty, true, hs::MODE_FORCE, true) : 0,
+                                o.precision == HS_FP32_REFINED ? march_smem(c->n1, c->ty64, true, hs::MODE_FORCE, true) : 0,
                                 c->smem_y, c->smem_z});
   if (need > (size_t)smem_optin) {
     delete c;
