@@ -115,6 +115,36 @@ __device__ __forceinline__ void tetra_strain_one(const T (&u)[2][2][2][3], const
   e[5] = E[5] + E[5] + g[0][1] + g[1][0];
 }
 
+// Engineering strain E + deps of one tetrahedron (tt = 0: T1, tt = 1: T2) from
+// the unscaled differences 2 D_i u_j, the factor 1/2 folded into one FMA.
+template <typename T>
+__device__ __forceinline__ void tetra_strain_fast(const T (&u)[2][2][2][3], const T* E, int tt, T* e) {
+  T g[3][3];  // g[i][j] = 2 D_i u_j
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (tt == 0) {
+      const T a = u[0][0][0][j], b = u[0][1][1][j], c = u[1][1][0][j], d = u[1][0][1][j];
+      const T p = a + b, q = c + d, m = a - b, n = c - d;
+      g[0][j] = p - q;
+      g[1][j] = m - n;
+      g[2][j] = m + n;
+    } else {
+      const T a = u[0][1][0][j], b = u[0][0][1][j], c = u[1][1][1][j], d = u[1][0][0][j];
+      const T p = a + b, q = c + d, m = b - a, n = d - c;
+      g[0][j] = p - q;
+      g[1][j] = m + n;
+      g[2][j] = n - m;
+    }
+  }
+  const T h = T(0.5);
+  e[0] = fma(h, g[0][0], E[0]);
+  e[1] = fma(h, g[1][1], E[1]);
+  e[2] = fma(h, g[2][2], E[2]);
+  e[3] = fma(h, g[1][2] + g[2][1], E[3] + E[3]);
+  e[4] = fma(h, g[0][2] + g[2][0], E[4] + E[4]);
+  e[5] = fma(h, g[0][1] + g[1][0], E[5] + E[5]);
+}
+
 // Shared-memory layout of k_march (host and device use the same function).
 struct MarchLayout {
   size_t ring, fbuf, stage, ids, src, edge, red, total;
@@ -463,10 +493,12 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
       }
       const bool acc_sig = xact && own_plane && jj <= TY;
       // ---- T1, then T2: strain, stress, adjoint stencil ----
+      // F is accumulated as 4 F (the 1/4 of the adjoint is applied when a row is
+      // complete); left-going vectors are sent with the sign their receiver applies.
 #pragma unroll
       for (int tt = 0; tt < 2; ++tt) {
         T ev[6], sv[6];
-        tetra_strain_one(u, E, tt, ev);
+        tetra_strain_fast(u, E, tt, ev);
         mat.stress(ph, ev, sv);
         if (!xact) {
 #pragma unroll
@@ -476,6 +508,7 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
 #pragma unroll
           for (int i = 0; i < 6; ++i) sacc[i] += sv[i];
         }
+        T l0[3], l1[3];
         // per force component k: (sigma_1k, sigma_2k, sigma_3k)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -483,32 +516,38 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
           const int i2 = (k == 0) ? 5 : (k == 1 ? 1 : 3);
           const int i3 = (k == 0) ? 4 : (k == 1 ? 3 : 2);
           const T Ps = sv[i1] + sv[i2], Ms = sv[i1] - sv[i2], Zs = sv[i3];
-          const T q = T(0.25);
-          T l0, l1;  // left-going: T1: a3 -> Fn[jj-2], a4 -> Fp[jj-1]; T2: a1 -> Fp[jj-2], a2 -> Fn[jj-1]
           if (tt == 0) {
-            if (jj - 1 < TY) Fn[jj - 1][k] += q * (Ps + Zs);        // T1 a1 (0,0,0)
-            if (jj - 2 >= 0) Fp[jj - 2][k] += q * (Ms - Zs);        // T1 a2 (0,-1,-1)
-            l0 = q * (Zs - Ps);                                     // T1 a3 (-1,-1,0)
-            l1 = -q * (Ms + Zs);                                    // T1 a4 (-1,0,-1)
+            if (jj - 1 < TY) Fn[jj - 1][k] += Ps + Zs;              // T1 a1 (0,0,0)
+            if (jj - 2 >= 0) Fp[jj - 2][k] += Ms - Zs;              // T1 a2 (0,-1,-1)
+            l0[k] = Zs - Ps;                                        // T1 a3 (-1,-1,0): +
+            l1[k] = Ms + Zs;                                        // T1 a4 (-1,0,-1): -
           } else {
-            if (jj - 2 >= 0) Fn[jj - 2][k] += q * (Ms + Zs);        // T2 a3 (0,-1,0)
-            if (jj - 1 < TY) Fp[jj - 1][k] += q * (Ps - Zs);        // T2 a4 (0,0,-1)
-            l0 = -q * (Ps + Zs);                                    // T2 a1 (-1,-1,-1)
-            l1 = q * (Zs - Ms);                                     // T2 a2 (-1,0,0)
+            if (jj - 2 >= 0) Fn[jj - 2][k] += Ms + Zs;              // T2 a3 (0,-1,0)
+            if (jj - 1 < TY) Fp[jj - 1][k] += Ps - Zs;              // T2 a4 (0,0,-1)
+            l0[k] = Ps + Zs;                                        // T2 a1 (-1,-1,-1): -
+            l1[k] = Zs - Ms;                                        // T2 a2 (-1,0,0): +
           }
-          const T g0 = __shfl_down_sync(0xffffffffu, l0, 1);
-          const T g1 = __shfl_down_sync(0xffffffffu, l1, 1);
-          if (lane == 0) {
-            edge[(warp * (TY + 1) + (jj - 1)) * 12 + (2 * tt) * 3 + k] = l0;
-            edge[(warp * (TY + 1) + (jj - 1)) * 12 + (2 * tt + 1) * 3 + k] = l1;
-          }
-          if (recv_shfl) {
+        }
+        T g0[3], g1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          g0[k] = __shfl_down_sync(0xffffffffu, l0[k], 1);
+          g1[k] = __shfl_down_sync(0xffffffffu, l1[k], 1);
+        }
+        if (lane == 0) {
+          T* ed = edge + (warp * (TY + 1) + (jj - 1)) * 12 + tt * 6;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) { ed[k] = l0[k]; ed[3 + k] = l1[k]; }
+        }
+        if (recv_shfl) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
             if (tt == 0) {
-              if (jj - 2 >= 0) Fn[jj - 2][k] += g0;
-              if (jj - 1 < TY) Fp[jj - 1][k] += g1;
+              if (jj - 2 >= 0) Fn[jj - 2][k] += g0[k];
+              if (jj - 1 < TY) Fp[jj - 1][k] -= g1[k];
             } else {
-              if (jj - 2 >= 0) Fp[jj - 2][k] += g0;
-              if (jj - 1 < TY) Fn[jj - 1][k] += g1;
+              if (jj - 2 >= 0) Fp[jj - 2][k] -= g0[k];
+              if (jj - 1 < TY) Fn[jj - 1][k] += g1[k];
             }
           }
         }
@@ -522,15 +561,19 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const T* e = edge + (src_warp * (TY + 1) + (jj - 1)) * 12;
-          if (jj - 2 >= 0) Fn[jj - 2][k] += e[0 * 3 + k];
-          if (jj - 1 < TY) Fp[jj - 1][k] += e[1 * 3 + k];
-          if (jj - 2 >= 0) Fp[jj - 2][k] += e[2 * 3 + k];
-          if (jj - 1 < TY) Fn[jj - 1][k] += e[3 * 3 + k];
+          if (jj - 2 >= 0) Fn[jj - 2][k] += e[0 * 3 + k];   // T1 a3
+          if (jj - 1 < TY) Fp[jj - 1][k] -= e[1 * 3 + k];   // T1 a4
+          if (jj - 2 >= 0) Fp[jj - 2][k] -= e[2 * 3 + k];   // T2 a1
+          if (jj - 1 < TY) Fn[jj - 1][k] += e[3 * 3 + k];   // T2 a2
         }
     }
     if (p > z0) {
-      // corner plane p-1 is complete
+      // corner plane p-1 is complete: undo the factor 4 of the accumulation
       const int zp = (p - 1) % n3;
+#pragma unroll
+      for (int r = 0; r < TY; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Fp[r][k] *= T(0.25);
       if (has_src && xact) {
         const float* sr = ssrc + (size_t)ib * 3 * TY * lay.n1s;
 #pragma unroll
