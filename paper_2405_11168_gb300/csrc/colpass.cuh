@@ -96,15 +96,17 @@ __device__ __forceinline__ void green_apply(const ColArgs<T>& a, int h1, int h2,
   }
 }
 
-template <typename T, int CT, int MODE>
+// LF > 0: the transformed length is LF and the block has NT threads, both
+// fixed at compile time (hot sizes); LF = 0: both taken at run time.
+template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArgs<T> a) {
   using C = typename cplx_t<T>::type;
   if (a.skip_if_done && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);  // [L][3][CT]
   const bool yaxis = (MODE == COL_Y_FWD || MODE == COL_Y_INV);
-  const int L = yaxis ? a.n2 : a.n3;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int L = LF > 0 ? LF : (yaxis ? a.n2 : a.n3);
+  const int tid = threadIdx.x, nthr = NT > 0 ? NT : (int)blockDim.x;
   const int x0 = blockIdx.x * CT;
   const int outer = blockIdx.y;
   const int ncol = min(CT, a.nh - x0);
@@ -133,7 +135,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
+  if constexpr (LF > 0) {
+    fft_fixed<LF, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, true, 1, W, -1>(sm, W, tw, tid, nthr);
+  } else if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
     HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
   } else {
     HS_FFT_COLS(false, sm, W, W, plan, tw, tid, nthr);
@@ -171,7 +175,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
       }
     }
     __syncthreads();
-    HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
+    if constexpr (LF > 0) {
+      fft_fixed<LF, true, true, 1, W, -1>(sm, W, tw, tid, nthr);
+    } else {
+      HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
+    }
   }
   for (int i = tid; i < L * W; i += nthr) {
     const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;

@@ -248,4 +248,99 @@ __host__ __device__ __forceinline__ int rpitch(int n) { return n + (n >> 3) + 1;
 #define HS_FFT_COLS(INV, buf, W, nseq, plan, tw, tid, nthr) \
   ::hs::fft_smem<INV, true>(buf, 1, W, -1, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
 
+
+// ---------------------------------------------------------------------------
+// Compile-time plans for the hot lengths: every stride, stage count and
+// radix is a constant, so the per-element index arithmetic folds away.
+// ---------------------------------------------------------------------------
+template <int L> struct FixedPlan { static constexpr int n = 0; };
+template <> struct FixedPlan<64> {
+  static constexpr int n = 2;
+  __host__ __device__ static constexpr int r(int i) { return 8; }
+};
+template <> struct FixedPlan<128> {
+  static constexpr int n = 3;
+  __host__ __device__ static constexpr int r(int i) { return i == 0 ? 8 : 4; }
+};
+template <> struct FixedPlan<256> {
+  static constexpr int n = 3;
+  __host__ __device__ static constexpr int r(int i) { return i == 2 ? 4 : 8; }
+};
+template <> struct FixedPlan<512> {
+  static constexpr int n = 3;
+  __host__ __device__ static constexpr int r(int i) { return 8; }
+};
+
+// one stage; sequence s element e at buf[s*SS + e*ES + (PS >= 0 ? e >> PS : 0)]
+template <int L, int R, int NS, int SS, int ES, int PS, bool INV, typename C>
+__device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, const C* __restrict__ tw, bool wsync) {
+  constexpr int T = L / kE;
+  constexpr int nb = L / R;
+  constexpr int KB = (nb + T - 1) / T;
+  constexpr int step = L / (NS * R);
+  C v[KB][R];
+  C* sb = buf + s * SS;
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int b = t + k * T;
+    if (active && b < nb) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int e = b + m * nb;
+        v[k][m] = sb[e * ES + (PS >= 0 ? (e >> PS) : 0)];
+      }
+    }
+  }
+  if (wsync) __syncwarp(); else __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int b = t + k * T;
+    if (active && b < nb) {
+      const int kk = b & (NS - 1);
+      const int pq = b / NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          C w = __ldg(tw + kk * m * step);
+          if (INV) w.y = -w.y;
+          v[k][m] = cmul(v[k][m], w);
+        }
+      }
+      Dft<R, INV, C>::run(v[k]);
+      const int base = pq * NS * R + kk;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int e = base + m * NS;
+        sb[e * ES + (PS >= 0 ? (e >> PS) : 0)] = v[k][m];
+      }
+    }
+  }
+  if (wsync) __syncwarp(); else __syncthreads();
+}
+
+template <int L, int ST, int NS, int SS, int ES, int PS, bool INV, typename C>
+__device__ __forceinline__ void stages_fixed(C* buf, int s, int t, bool active, const C* __restrict__ tw,
+                                             bool wsync) {
+  if constexpr (ST < FixedPlan<L>::n) {
+    constexpr int R = FixedPlan<L>::r(ST);
+    stage_fixed<L, R, NS, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
+    stages_fixed<L, ST + 1, NS * R, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
+  }
+}
+
+// Same contract as fft_smem with L, the strides and the mapping fixed at compile time.
+template <int L, bool INV, bool COLMAP, int SS, int ES, int PS, typename C>
+__device__ __forceinline__ void fft_fixed(C* buf, int nseq, const C* __restrict__ tw, int tid, int nthreads) {
+  constexpr int T = L / kE;
+  const int G = nthreads / T;
+  const bool wsync = !COLMAP && T <= 32 && (32 % T) == 0 && (nthreads % 32) == 0;
+  for (int g0 = 0; g0 < nseq; g0 += G) {
+    const int sl = COLMAP ? (tid % G) : (tid / T);
+    const int t = COLMAP ? (tid / G) : (tid % T);
+    const int s = g0 + sl;
+    const bool active = (COLMAP ? (t < T) : (sl < G)) && s < nseq;
+    stages_fixed<L, 0, 1, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
+  }
+}
+
 }  // namespace hs

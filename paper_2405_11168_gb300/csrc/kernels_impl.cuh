@@ -46,33 +46,59 @@ static cudaError_t march_real(const MarchArgs<T>& a, bool iso, int ty, int mode,
   }
 }
 
-template <typename T, int CT, int MODE>
+template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
 static cudaError_t col_one(const ColArgs<T>& a, dim3 g, int nthr, size_t smem, cudaStream_t s) {
-  auto k = k_col<T, CT, MODE>;
+  auto k = k_col<T, CT, MODE, LF, NT>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<g, nthr, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int CT>
+template <typename T, int CT, int LF = 0, int NT = 0>
 static cudaError_t col_ct(const ColArgs<T>& a, int mode, dim3 g, int nthr, size_t smem, cudaStream_t s) {
   switch (mode) {
-    case COL_Y_FWD: return col_one<T, CT, COL_Y_FWD>(a, g, nthr, smem, s);
-    case COL_Y_INV: return col_one<T, CT, COL_Y_INV>(a, g, nthr, smem, s);
-    case COL_Z_GREEN: return col_one<T, CT, COL_Z_GREEN>(a, g, nthr, smem, s);
-    case COL_Z_INV_STATE: return col_one<T, CT, COL_Z_INV_STATE>(a, g, nthr, smem, s);
+    case COL_Y_FWD: return col_one<T, CT, COL_Y_FWD, LF, NT>(a, g, nthr, smem, s);
+    case COL_Y_INV: return col_one<T, CT, COL_Y_INV, LF, NT>(a, g, nthr, smem, s);
+    case COL_Z_GREEN: return col_one<T, CT, COL_Z_GREEN, LF, NT>(a, g, nthr, smem, s);
+    case COL_Z_INV_STATE: return col_one<T, CT, COL_Z_INV_STATE, LF, NT>(a, g, nthr, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T, int MODE>
+// transformed length of a column pass
+template <typename T> static int col_length(const ColArgs<T>& a, int mode) {
+  return (mode == COL_Y_FWD || mode == COL_Y_INV) ? a.n2 : a.n3;
+}
+
+// compile-time variants for the default tile and block size at the hot lengths
+template <typename T, int CT, int NT>
+static cudaError_t col_dispatch(const ColArgs<T>& a, int mode, dim3 g, int nthr, size_t smem, cudaStream_t s) {
+  const int L = col_length(a, mode);
+  if (nthr == NT) {
+    if (L == 256) return col_ct<T, CT, 256, NT>(a, mode, g, nthr, smem, s);
+    if (L == 512) return col_ct<T, CT, 512, NT>(a, mode, g, nthr, smem, s);
+  }
+  return col_ct<T, CT>(a, mode, g, nthr, smem, s);
+}
+
+template <typename T, int MODE, int LF = 0>
 static cudaError_t row_one(const RowArgs<T>& a, int nb, int nthr, size_t smem, cudaStream_t s) {
-  auto k = k_row<T, MODE>;
+  auto k = k_row<T, MODE, LF>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<nb, nthr, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// compile-time variants for 256-thread blocks at the hot lengths
+template <typename T, int MODE>
+static cudaError_t row_dispatch(const RowArgs<T>& a, int nb, int nthr, size_t smem, cudaStream_t s) {
+  if (nthr == 256) {
+    if (a.n1 == 256) return row_one<T, MODE, 256>(a, nb, nthr, smem, s);
+    if (a.n1 == 512) return row_one<T, MODE, 512>(a, nb, nthr, smem, s);
+  }
+  return row_one<T, MODE>(a, nb, nthr, smem, s);
 }
 
 template <typename T>
@@ -103,7 +129,9 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
 
 }  // namespace hs
 
-#define HS_INSTANTIATE(T, REALOK, CT)                                                                    \
+// CT: the wider column tile (CT / 2 is the default); NT: the default
+// column-pass block size, which gets compile-time variants at hot lengths.
+#define HS_INSTANTIATE(T, REALOK, CT, NT)                                                                 \
   namespace hs {                                                                                         \
   template <>                                                                                            \
   cudaError_t launch_march<T>(const MarchArgs<T>& a, bool iso, int ty, int mode, bool real, dim3 grid,  \
@@ -124,7 +152,7 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     if (a.buf == nullptr || a.tw == nullptr || ((mode == COL_Z_GREEN || mode == COL_Z_INV_STATE) && a.S == nullptr)) \
       return cudaErrorInvalidValue;                                                                      \
     if (ct == (CT)) return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                  \
-    if (ct == (CT) / 2) return col_ct<T, (CT) / 2>(a, mode, grid, nthr, smem, s);                        \
+    if (ct == (CT) / 2) return col_dispatch<T, (CT) / 2, NT>(a, mode, grid, nthr, smem, s);              \
     return cudaErrorInvalidValue;                                                                        \
   }                                                                                                      \
   template <>                                                                                            \
@@ -132,7 +160,8 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     if (a.tw == nullptr || (mode == ROW_C2R ? (a.spec_in == nullptr || (a.real_out == nullptr && a.acc64 == nullptr)) \
                                             : (a.real_in == nullptr || a.spec_out == nullptr)))         \
       return cudaErrorInvalidValue;                                                                      \
-    return mode == ROW_C2R ? row_one<T, ROW_C2R>(a, nb, nthr, smem, s) : row_one<T, ROW_R2C>(a, nb, nthr, smem, s); \
+    return mode == ROW_C2R ? row_dispatch<T, ROW_C2R>(a, nb, nthr, smem, s)                             \
+                           : row_dispatch<T, ROW_R2C>(a, nb, nthr, smem, s);                            \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t launch_state_export<T>(const typename cplx_t<T>::type* S, double2* out, int n2, int n3,     \

@@ -36,13 +36,15 @@ __device__ __forceinline__ void group_sync(bool wsync) {
   else __syncthreads();
 }
 
-template <typename T, int MODE>
+// LF > 0: N1 = LF and 256 threads per block, fixed at compile time (hot
+// sizes); LF = 0: both taken at run time.
+template <typename T, int MODE, int LF = 0>
 __global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
   using C = typename cplx_t<T>::type;
   if (a.skip_if_done && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n1 = a.n1, P = a.P, nh = n1 / 2 + 1, half = n1 / 2;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int n1 = LF > 0 ? LF : a.n1, P = a.P, nh = n1 / 2 + 1, half = n1 / 2;
+  const int tid = threadIdx.x, nthr = LF > 0 ? 256 : (int)blockDim.x;
   const int T8 = (n1 + kE - 1) / kE;          // threads per sequence
   const int G = nthr / T8;                     // sequences per block pass
   const int grp = tid / T8, t = tid - grp * T8;
@@ -71,8 +73,12 @@ __global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
         }
       }
       group_sync(wsync);
-      fft_smem<true, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
-                            tid, nthr);
+      if constexpr (LF > 0) {
+        fft_fixed<LF, true, false, LF + LF / 8 + 1, 1, 3>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+      } else {
+        fft_smem<true, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
+                              tid, nthr);
+      }
       group_sync(wsync);
       if (act) {
         for (int x = t; x < n1; x += T8) {
@@ -100,8 +106,12 @@ __global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
         }
       }
       group_sync(wsync);
-      fft_smem<false, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
-                             tid, nthr);
+      if constexpr (LF > 0) {
+        fft_fixed<LF, false, false, LF + LF / 8 + 1, 1, 3>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+      } else {
+        fft_smem<false, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
+                              tid, nthr);
+      }
       group_sync(wsync);
       if (act) {
         C* A = a.spec_out + r0 * P;

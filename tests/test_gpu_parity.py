@@ -103,6 +103,27 @@ def test_z_chunking_and_column_groups(hs, prec, zchunk):
     assert rel(out["sig"].cpu().numpy(), s_ref) < tol
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("grid", [(256, 512, 4), (512, 6, 256), (4, 256, 512)])
+def test_hot_length_compiled_variants(hs, prec, grid):
+    """Axis lengths 256 and 512 run FFT kernels whose plan, strides and block
+    size are fixed at compile time (rows along x, columns along y and z); each
+    such kernel here meets a generic one on another axis.  Same iterates as
+    the oracle."""
+    ids = synth.random_phase_map(grid, 2, seed=sum(grid))
+    table = synth.two_phase_table(1.0, 0.3, 8.0, 0.3)
+    C0 = synth.isotropic_voigt(4.5, 0.3)
+    s = hs.Solver(ids, table, C0=C0, precision=prec)
+    out = s.solve(E_MIX, tol=0.0, max_iter=3)
+    ref = T.solve_alg1(ids, table, T.stiffness_tensor(C0), T.strain_tensor_from_voigt(E_MIX), tol=0.0, max_iter=3)
+    tol = 1e-10 if prec == 0 else 2e-5
+    np.testing.assert_allclose(s.err_history(), ref.errs, rtol=tol)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < tol
+    assert rel(out["sig"].cpu().numpy(), s_ref) < tol
+    s.close()
+
+
 def _corner_state_to_paper(uc, grid):
     n1, n2, n3 = grid
     q1, q2, q3 = T.q_vectors(grid)
