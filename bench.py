@@ -186,6 +186,20 @@ def cpu_sample(ids, table, workers=None):
     return one
 
 
+def combine_over_ranks(ms, iters, device, world):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all ranks'."""
+    if world <= 1:
+        return float(ms), float(iters)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters)], device=device, dtype=torch.float64)
+    dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(it.item())
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -297,15 +311,7 @@ def run_ours(args):
             a, b = prof.get(k, (0.0, 0))
             prof[k] = (a + t, b + n)
         s.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        it = torch.tensor([total_iters], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
-        total_iters_all = float(it.item())
-    else:
-        total_iters_all = float(total_iters)
+    ms, total_iters_all = combine_over_ranks(ms, total_iters, dev, world)
     value = total_iters_all * N / (ms / 1e3)
     launches = int(sum(n for (_, n) in prof.values()))
 
