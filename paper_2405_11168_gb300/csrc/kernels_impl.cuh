@@ -46,6 +46,41 @@ static cudaError_t march_real(const MarchArgs<T>& a, bool iso, int ty, int mode,
   }
 }
 
+template <int TY, class MATP, int MODE>
+static cudaError_t stencil_one(const MarchArgs<float>& a, const MATP& m, dim3 g, int nthr, size_t smem,
+                               cudaStream_t s) {
+  auto k = k_stencil<TY, MATP, MODE>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<g, nthr, smem, s>>>(a, m);
+  return cudaGetLastError();
+}
+
+template <int TY>
+static cudaError_t stencil_ty(const MarchArgs<float>& a, bool iso, int mode, dim3 g, int nthr, size_t smem,
+                              cudaStream_t s) {
+  if (iso) {
+    MatIsoP m{a.mat};
+    if (mode == MODE_FORCE) return stencil_one<TY, MatIsoP, MODE_FORCE>(a, m, g, nthr, smem, s);
+    return stencil_one<TY, MatIsoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
+  }
+  MatAnisoP m{a.mat};
+  if (mode == MODE_FORCE) return stencil_one<TY, MatAnisoP, MODE_FORCE>(a, m, g, nthr, smem, s);
+  return stencil_one<TY, MatAnisoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
+}
+
+// FP32 real-space pass (FORCE / FIELDS on a real displacement field)
+static cudaError_t stencil_f32(const MarchArgs<float>& a, bool iso, int ty, int mode, dim3 g, int nthr,
+                               size_t smem, cudaStream_t s) {
+  if (mode != MODE_FORCE && mode != MODE_FIELDS) return cudaErrorInvalidValue;
+  switch (ty) {
+    case 2: return stencil_ty<2>(a, iso, mode, g, nthr, smem, s);
+    case 4: return stencil_ty<4>(a, iso, mode, g, nthr, smem, s);
+    case 8: return stencil_ty<8>(a, iso, mode, g, nthr, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
 static cudaError_t col_one(const ColArgs<T>& a, dim3 g, int nthr, size_t smem, cudaStream_t s) {
   auto k = k_col<T, CT, MODE, LF, NT>;
@@ -53,6 +88,16 @@ static cudaError_t col_one(const ColArgs<T>& a, dim3 g, int nthr, size_t smem, c
   if (e != cudaSuccess) return e;
   k<<<g, nthr, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// real-displacement passes: the packed FP32 kernel, or k_march for FP64
+static inline cudaError_t march_real_dispatch(const MarchArgs<float>& a, bool iso, int ty, int mode, dim3 g,
+                                              int nthr, size_t smem, cudaStream_t s) {
+  return stencil_f32(a, iso, ty, mode, g, nthr, smem, s);
+}
+static inline cudaError_t march_real_dispatch(const MarchArgs<double>& a, bool iso, int ty, int mode, dim3 g,
+                                              int nthr, size_t smem, cudaStream_t s) {
+  return march_real<double, true>(a, iso, ty, mode, g, nthr, smem, s);
 }
 
 template <typename T, int CT, int LF = 0, int NT = 0>
@@ -143,7 +188,7 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     if (mode == MODE_EMIT && a.u64 == nullptr) return cudaErrorInvalidValue;                             \
     if (mode == MODE_FORCE && !real && a.out == nullptr) return cudaErrorInvalidValue;                   \
     if (mode == MODE_FIELDS && (a.eps_out == nullptr || a.sig_out == nullptr)) return cudaErrorInvalidValue; \
-    if (real) return march_real<T, true>(a, iso, ty, mode, grid, nthr, smem, s);                         \
+    if (real) return march_real_dispatch(a, iso, ty, mode, grid, nthr, smem, s);                         \
     return march_real<T, false>(a, iso, ty, mode, grid, nthr, smem, s);                                  \
   }                                                                                                      \
   template <>                                                                                            \

@@ -6,6 +6,7 @@
 #include "colpass.cuh"
 #include "march.cuh"
 #include "rowpass.cuh"
+#include "stencil.cuh"
 
 namespace hs {
 
