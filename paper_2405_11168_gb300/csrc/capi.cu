@@ -218,8 +218,8 @@ struct hs_ctx {
   dim3 grid_m64;
   int ct, nthr_y, nthr_z;
   bool xfuse;
-  int nthr_row, nblk_row;
-  size_t smem_row;
+  int nthr_row, nblk_row[2];  // [ROW_C2R], [ROW_R2C]
+  size_t smem_row[2];
   size_t smem_y, smem_z;
   dim3 grid_y, grid_z;
   bool warm;
@@ -408,7 +408,7 @@ template <typename T> hs_status launch_rows(hs_ctx* c, int mode, double* acc64, 
   cudaError_t e;
   {
     LaunchScope ls(c, acc64 ? HS_K_OTHER : (mode == hs::ROW_C2R ? HS_K_XINV : HS_K_XFWD));
-    e = hs::launch_row<T>(a, mode, c->nblk_row, c->nthr_row, c->smem_row, c->stream);
+    e = hs::launch_row<T>(a, mode, c->nblk_row[mode], c->nthr_row, c->smem_row[mode], c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_row");
   return HS_OK;
@@ -871,14 +871,8 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
   c->smem_z = (size_t)c->n3 * 3 * c->ct * cs;
   c->xfuse = (o.xfuse == 1);
-  {
-    const int T8 = (c->n1 + hs::kE - 1) / hs::kE;
-    c->nthr_row = 256;
-    const int G = c->nthr_row / T8;
-    const size_t nseq = (size_t)3 * c->n2 * c->n3 / 2;
-    c->nblk_row = (int)std::min<size_t>((nseq + G - 1) / G, 65535);
-    c->smem_row = (size_t)G * hs::rpitch(c->n1) * cs;
-  }
+  c->nthr_row = 256;
+  for (int m = 0; m < 2; ++m) c->smem_row[m] = hs::row_layout(m, c->n1, c->P, c->nthr_row, c->f64 ? 8 : 4).total;
   const int xtiles = (c->nh + c->ct - 1) / c->ct;
   c->grid_y = dim3(xtiles, c->n3);
   c->grid_z = dim3(xtiles, c->n2);
@@ -906,12 +900,31 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   }
   const size_t need = std::max({c->xfuse ? march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, false, true)
                                           : march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, true, true),
-                                c->smem_row,
+                                c->smem_row[0], c->smem_row[1],
                                 o.precision == HS_FP32_REFINED ? march_smem(c->n1, c->ty64, true, hs::MODE_FORCE, true) : 0,
                                 c->smem_y, c->smem_z});
   if (need > (size_t)smem_optin) {
     delete c;
     return fail(nullptr, HS_ERR_UNSUPPORTED_SIZE, "grid too large for shared-memory tiles");
+  }
+  // persistent row passes: as many blocks as stay resident, at most one per batch
+  {
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int T8 = (c->n1 + hs::kE - 1) / hs::kE;
+    const size_t G = (size_t)(c->nthr_row / T8);
+    const size_t nbatch = ((size_t)3 * c->n2 * c->n3 / 2 + G - 1) / G;
+    for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+      int per_sm = 0;
+      e = c->f64 ? hs::row_blocks_per_sm<double>(m, c->n1, c->nthr_row, c->smem_row[m], &per_sm)
+                 : hs::row_blocks_per_sm<float>(m, c->n1, c->nthr_row, c->smem_row[m], &per_sm);
+      c->nblk_row[m] = (int)std::min<size_t>(nbatch, (size_t)std::max(1, per_sm) * std::max(1, nsm));
+    }
+    if (e != cudaSuccess) {
+      hs_status st = cuda_fail(nullptr, e, "row pass occupancy");
+      delete c;
+      return st;
+    }
   }
 
   // twiddles / phase tables in kernel precision

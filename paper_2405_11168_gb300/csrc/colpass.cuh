@@ -96,6 +96,48 @@ __device__ __forceinline__ void green_apply(const ColArgs<T>& a, int h1, int h2,
   }
 }
 
+// Green update of one z-pass tile (Algorithm 1 step 5): sm holds the forward
+// transformed force F(q) of the tile; the state u(q) is read from and written
+// to a.S, and the new u(q) replaces F(q) in sm for the inverse transform.
+template <typename T, int CT>
+__device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T>::type* sm, size_t base,
+                                          size_t rstride, size_t cstride, int x0, int outer, int ncol, int L,
+                                          int tid, int nthr) {
+  using C = typename cplx_t<T>::type;
+  constexpr int W = 3 * CT;
+  constexpr int GU = 4;  // points per thread per batch: state loads issued together
+  for (int i0 = tid; i0 < L * CT; i0 += GU * nthr) {
+    C U[GU][3];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int i = i0 + u * nthr;
+      const int z = i / CT, col = i - z * CT;
+      if (i < L * CT && col < ncol) {
+        const size_t g = base + z * rstride + col;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) U[u][c] = a.S[c * cstride + g];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int i = i0 + u * nthr;
+      const int z = i / CT, col = i - z * CT;
+      if (i < L * CT && col < ncol) {
+        C F[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) F[c] = sm[z * W + c * CT + col];
+        green_apply<T>(a, x0 + col, outer, z, F, U[u]);
+        const size_t g = base + z * rstride + col;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          a.S[c * cstride + g] = U[u][c];
+          sm[z * W + c * CT + col] = U[u][c];
+        }
+      }
+    }
+  }
+}
+
 // LF > 0: the transformed length is LF and the block has NT threads, both
 // fixed at compile time (hot sizes); LF = 0: both taken at run time.
 template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
@@ -118,10 +160,30 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   const FftPlan plan = a.plan;
   const C* __restrict__ tw = a.tw;
   constexpr int W = 3 * CT;
+  const int ccols = min(CT, a.P - x0);
+  if constexpr (LF > 0) {
+    // first stage straight from global memory, last stage straight back
+    ColIO<C> io;
+    io.cstride = cstride;
+    io.rstride = rstride;
+    io.ccols = ccols;
+    io.ncol = ncol;
+    io.gout = a.buf + base;
+    if (MODE == COL_Z_GREEN) {
+      io.gin = a.buf + base;
+      fft_col_fixed<LF, W, CT, false, true, false>(sm, io, tw, tid, nthr);
+      col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+      __syncthreads();
+      fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, nthr);
+    } else {
+      io.gin = src + base;
+      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, true, true>(sm, io, tw, tid, nthr);
+    }
+    return;
+  }
   // tile load: 16-byte asynchronous copies; columns past the row pitch are zero
   constexpr int EPC = 16 / (int)sizeof(C);  // complex values per 16-byte chunk
   constexpr int CPR = CT / EPC;             // chunks per (row, component)
-  const int ccols = min(CT, a.P - x0);
   for (int i = tid; i < L * 3 * CPR; i += nthr) {
     const int e = i / (3 * CPR), rem = i - e * (3 * CPR), c = rem / CPR, col = (rem - c * CPR) * EPC;
     C* dst = sm + e * W + c * CT + col;
@@ -135,51 +197,15 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  if constexpr (LF > 0) {
-    fft_fixed<LF, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, true, 1, W, -1>(sm, W, tw, tid, nthr);
-  } else if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
+  if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
     HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
   } else {
     HS_FFT_COLS(false, sm, W, W, plan, tw, tid, nthr);
   }
   if (MODE == COL_Z_GREEN) {
-    constexpr int GU = 4;  // points per thread per batch: state loads issued together
-    for (int i0 = tid; i0 < L * CT; i0 += GU * nthr) {
-      C U[GU][3];
-#pragma unroll
-      for (int u = 0; u < GU; ++u) {
-        const int i = i0 + u * nthr;
-        const int z = i / CT, col = i - z * CT;
-        if (i < L * CT && col < ncol) {
-          const size_t g = base + z * rstride + col;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) U[u][c] = a.S[c * cstride + g];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < GU; ++u) {
-        const int i = i0 + u * nthr;
-        const int z = i / CT, col = i - z * CT;
-        if (i < L * CT && col < ncol) {
-          C F[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) F[c] = sm[z * W + c * CT + col];
-          green_apply<T>(a, x0 + col, outer, z, F, U[u]);
-          const size_t g = base + z * rstride + col;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            a.S[c * cstride + g] = U[u][c];
-            sm[z * W + c * CT + col] = U[u][c];
-          }
-        }
-      }
-    }
+    col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
     __syncthreads();
-    if constexpr (LF > 0) {
-      fft_fixed<LF, true, true, 1, W, -1>(sm, W, tw, tid, nthr);
-    } else {
-      HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
-    }
+    HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
   }
   for (int i = tid; i < L * W; i += nthr) {
     const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;

@@ -144,6 +144,22 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Bulk shared -> global copies (cp.async.bulk, bulk-group completion).  Both
+// addresses 16-byte aligned, size a multiple of 16.  The writes that filled
+// the shared source must be made visible to the async proxy first
+// (fence_async_smem() by every writing thread, then a barrier).
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, unsigned bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(ssrc));
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// the shared sources of all committed bulk copies may be overwritten
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// all committed bulk copies are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 constexpr int kMaxStages = 8;
 // Radix of each stage packed 4 bits per stage (stage 0 in the low bits), so
 // the plan is three plain integers and never needs indexed storage.
@@ -271,7 +287,17 @@ template <> struct FixedPlan<512> {
   __host__ __device__ static constexpr int r(int i) { return 8; }
 };
 
-// one stage; sequence s element e at buf[s*SS + e*ES + (PS >= 0 ? e >> PS : 0)]
+// Position of element e inside a sequence: e*ES + (e >> PS) for PS >= 0, e*ES
+// for PS = -1, and for PS = -2 (rows, ES = 1, length a multiple of 16) the XOR
+// swizzle e ^ (((e >> 3) ^ (e >> 7)) & 15), which keeps the 64-bit accesses of
+// every stage of the fixed 64..512 plans (nearly) free of bank conflicts.
+template <int ES, int PS> __host__ __device__ __forceinline__ int seq_pos(int e) {
+  if constexpr (PS == -2) return e ^ (((e >> 3) ^ (e >> 7)) & 15);
+  else return e * ES + (PS >= 0 ? (e >> PS) : 0);
+}
+__host__ __device__ __forceinline__ int rswz(int e) { return seq_pos<1, -2>(e); }
+
+// one stage; sequence s element e at buf[s*SS + seq_pos<ES, PS>(e)]
 template <int L, int R, int NS, int SS, int ES, int PS, bool INV, typename C>
 __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, const C* __restrict__ tw, bool wsync) {
   constexpr int T = L / kE;
@@ -287,7 +313,7 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int e = b + m * nb;
-        v[k][m] = sb[e * ES + (PS >= 0 ? (e >> PS) : 0)];
+        v[k][m] = sb[seq_pos<ES, PS>(e)];
       }
     }
   }
@@ -311,7 +337,7 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int e = base + m * NS;
-        sb[e * ES + (PS >= 0 ? (e >> PS) : 0)] = v[k][m];
+        sb[seq_pos<ES, PS>(e)] = v[k][m];
       }
     }
   }
@@ -340,6 +366,107 @@ __device__ __forceinline__ void fft_fixed(C* buf, int nseq, const C* __restrict_
     const int s = g0 + sl;
     const bool active = (COLMAP ? (t < T) : (sl < G)) && s < nseq;
     stages_fixed<L, 0, 1, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Column-tile FFTs with global-memory ends: sequence s = c * CT + col (c the
+// field component, col the column in the tile) is column col of component c,
+// element e of it lives at g[c * cstride + col + e * rstride] in global memory
+// and at sm[e * W + s] in the shared tile.  IN_G: the first stage reads its
+// butterfly inputs from global memory (columns >= ccols read as zero); OUT_G:
+// the last stage writes its outputs to global memory (columns < ncol only).
+// Every other stage goes through the shared tile as in fft_fixed (COLMAP).
+// ---------------------------------------------------------------------------
+template <typename C> struct ColIO {
+  const C* gin;
+  C* gout;
+  size_t cstride, rstride;
+  int ccols, ncol;
+};
+
+template <int L, int R, int NS, int W, int CT, bool INV, bool FROM_G, bool TO_G, typename C>
+__device__ __forceinline__ void stage_col(C* sm, const ColIO<C>& io, int s, int t, bool active,
+                                          const C* __restrict__ tw) {
+  constexpr int T = L / kE;
+  constexpr int nb = L / R;
+  constexpr int KB = (nb + T - 1) / T;
+  constexpr int step = L / (NS * R);
+  const int c = s / CT, col = s - c * CT;
+  C v[KB][R];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int b = t + k * T;
+    if (active && b < nb) {
+      if (FROM_G) {
+        const C* gp = io.gin + c * io.cstride + col;
+        const bool ok = col < io.ccols;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int e = b + m * nb;
+          v[k][m] = ok ? gp[(size_t)e * io.rstride] : cmk<C>(0, 0);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[k][m] = sm[(b + m * nb) * W + s];
+      }
+    }
+  }
+  if (!FROM_G) __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int b = t + k * T;
+    if (active && b < nb) {
+      const int kk = b & (NS - 1);
+      const int pq = b / NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          C w = __ldg(tw + kk * m * step);
+          if (INV) w.y = -w.y;
+          v[k][m] = cmul(v[k][m], w);
+        }
+      }
+      Dft<R, INV, C>::run(v[k]);
+      const int base = pq * NS * R + kk;
+      if (TO_G) {
+        if (col < io.ncol) {
+          C* gp = io.gout + c * io.cstride + col;
+#pragma unroll
+          for (int m = 0; m < R; ++m) gp[(size_t)(base + m * NS) * io.rstride] = v[k][m];
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < R; ++m) sm[(base + m * NS) * W + s] = v[k][m];
+      }
+    }
+  }
+  if (!TO_G) __syncthreads();
+}
+
+template <int L, int ST, int NS, int W, int CT, bool INV, bool IN_G, bool OUT_G, typename C>
+__device__ __forceinline__ void stages_col(C* sm, const ColIO<C>& io, int s, int t, bool active,
+                                           const C* __restrict__ tw) {
+  if constexpr (ST < FixedPlan<L>::n) {
+    constexpr int R = FixedPlan<L>::r(ST);
+    constexpr bool FIRST = (ST == 0), LAST = (ST + 1 == FixedPlan<L>::n);
+    stage_col<L, R, NS, W, CT, INV, IN_G && FIRST, OUT_G && LAST>(sm, io, s, t, active, tw);
+    stages_col<L, ST + 1, NS * R, W, CT, INV, IN_G, OUT_G>(sm, io, s, t, active, tw);
+  }
+}
+
+// FFT of the W = 3 * CT columns of a tile; lanes walk across columns (COLMAP).
+template <int L, int W, int CT, bool INV, bool IN_G, bool OUT_G, typename C>
+__device__ __forceinline__ void fft_col_fixed(C* sm, const ColIO<C>& io, const C* __restrict__ tw, int tid,
+                                              int nthreads) {
+  constexpr int T = L / kE;
+  const int G = nthreads / T;
+  for (int g0 = 0; g0 < W; g0 += G) {
+    const int sl = tid % G, t = tid / G;
+    const int s = g0 + sl;
+    const bool active = t < T && s < W;
+    stages_col<L, 0, 1, W, CT, INV, IN_G, OUT_G>(sm, io, s, t, active, tw);
   }
 }
 

@@ -136,6 +136,23 @@ static cudaError_t row_one(const RowArgs<T>& a, int nb, int nthr, size_t smem, c
   return cudaGetLastError();
 }
 
+template <typename T, int MODE, int LF = 0>
+static cudaError_t row_occ_one(int nthr, size_t smem, int* n) {
+  auto k = k_row<T, MODE, LF>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k, nthr, smem);
+}
+
+template <typename T, int MODE>
+static cudaError_t row_occ(int n1, int nthr, size_t smem, int* n) {
+  if (nthr == 256) {
+    if (n1 == 256) return row_occ_one<T, MODE, 256>(nthr, smem, n);
+    if (n1 == 512) return row_occ_one<T, MODE, 512>(nthr, smem, n);
+  }
+  return row_occ_one<T, MODE>(nthr, smem, n);
+}
+
 // compile-time variants for 256-thread blocks at the hot lengths
 template <typename T, int MODE>
 static cudaError_t row_dispatch(const RowArgs<T>& a, int nb, int nthr, size_t smem, cudaStream_t s) {
@@ -207,6 +224,10 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
       return cudaErrorInvalidValue;                                                                      \
     return mode == ROW_C2R ? row_dispatch<T, ROW_C2R>(a, nb, nthr, smem, s)                             \
                            : row_dispatch<T, ROW_R2C>(a, nb, nthr, smem, s);                            \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t row_blocks_per_sm<T>(int mode, int n1, int nthr, size_t smem, int* n) {                     \
+    return mode == ROW_C2R ? row_occ<T, ROW_C2R>(n1, nthr, smem, n) : row_occ<T, ROW_R2C>(n1, nthr, smem, n); \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t launch_state_export<T>(const typename cplx_t<T>::type* S, double2* out, int n2, int n3,     \

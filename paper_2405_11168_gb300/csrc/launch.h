@@ -23,6 +23,10 @@ cudaError_t launch_col(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nth
 template <typename T>
 cudaError_t launch_row(const RowArgs<T>& a, int mode, int nblocks, int nthr, size_t smem, cudaStream_t s);
 
+// resident blocks per SM of the row pass (persistent grid sizing)
+template <typename T>
+cudaError_t row_blocks_per_sm(int mode, int n1, int nthr, size_t smem, int* n);
+
 // u8 phase ids -> u16
 cudaError_t launch_ids_u8_to_u16(const uint8_t* in, uint16_t* out, size_t n, cudaStream_t s);
 // largest id into *out (int, must start at 0)

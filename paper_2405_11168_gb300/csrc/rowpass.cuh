@@ -9,7 +9,9 @@
 //   A[k] = (Z[k] + conj Z[N1-k]) / 2 and B[k] = (Z[k] - conj Z[N1-k]) / (2i).
 //
 // A group of T = N1/8 threads owns one pair of rows at a time; for N1 <= 256
-// the group lies inside one warp and needs only warp barriers.
+// the group lies inside one warp and needs only warp barriers.  Blocks are
+// persistent and stage their next batch of input rows with cp.async while
+// transforming the current one.
 #pragma once
 #include "common.cuh"
 
@@ -36,53 +38,136 @@ __device__ __forceinline__ void group_sync(bool wsync) {
   else __syncthreads();
 }
 
+// Shared memory of k_row: FFT rows z[G][rpitch(n1)], then two staging buffers
+// of one batch (2G rows) each; a staging buffer holds the batch's input rows,
+// then (bulk-store path) its output rows.  Host and device use the same function.
+struct RowLayout {
+  int G;            // sequences (row pairs) per batch
+  size_t zbytes;    // z rows
+  size_t rowbytes;  // bytes of one input row (C2R: P complex; R2C: n1 real)
+  size_t outbytes;  // bytes of one output row (C2R: n1 real; R2C: P complex)
+  size_t stage;     // bytes of one staging buffer
+  size_t total;
+};
+__host__ __device__ inline RowLayout row_layout(int mode, int n1, int P, int nthr, int tsize) {
+  RowLayout L;
+  const int T8 = (n1 + kE - 1) / kE;
+  L.G = nthr / T8;
+  L.zbytes = (((size_t)L.G * rpitch(n1) * 2 * tsize) + 15) & ~(size_t)15;
+  L.rowbytes = (mode == ROW_C2R) ? (size_t)P * 2 * tsize : (size_t)n1 * tsize;
+  L.outbytes = (mode == ROW_C2R) ? (size_t)n1 * tsize : (size_t)P * 2 * tsize;
+  const size_t rb = L.rowbytes > L.outbytes ? L.rowbytes : L.outbytes;
+  L.stage = ((2 * (size_t)L.G * rb) + 15) & ~(size_t)15;
+  L.total = L.zbytes + 2 * L.stage;
+  return L;
+}
+
+// Asynchronous copy of batch b (input rows 2bG .. 2bG + 2G - 1, clipped to
+// nrows) into staging buffer `buf`: the rows are one contiguous byte range.
+template <typename T, int MODE>
+__device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& L, unsigned char* smraw, int b,
+                                          int buf) {
+  const size_t r0 = 2 * (size_t)b * L.G;
+  const size_t nr = min((size_t)2 * L.G, (size_t)a.nrows - r0);
+  const unsigned char* src = (MODE == ROW_C2R) ? reinterpret_cast<const unsigned char*>(a.spec_in)
+                                               : reinterpret_cast<const unsigned char*>(a.real_in);
+  src += r0 * L.rowbytes;
+  unsigned char* dst = smraw + L.zbytes + (size_t)buf * L.stage;
+  const size_t bytes = nr * L.rowbytes;
+  if ((L.rowbytes & 15) == 0) {
+    const int nch = (int)(bytes >> 4);
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) cp_async16(dst + 16 * i, src + 16 * i);
+  } else {
+    // rows of a size that is not a multiple of 16 bytes (R2C with N1 % 4 != 0): element copies
+    const T* s = reinterpret_cast<const T*>(src);
+    T* d = reinterpret_cast<T*>(dst);
+    for (size_t i = threadIdx.x; i < bytes / sizeof(T); i += blockDim.x) d[i] = s[i];
+  }
+  cp_async_commit();
+}
+
+// Persistent: block j transforms batches j, j + gridDim.x, ...; the copy of the
+// next batch runs while the current one is transformed.
 // LF > 0: N1 = LF and 256 threads per block, fixed at compile time (hot
 // sizes); LF = 0: both taken at run time.
 template <typename T, int MODE, int LF = 0>
-__global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowArgs<T> a) {
   using C = typename cplx_t<T>::type;
   if (a.skip_if_done && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = LF > 0 ? LF : a.n1, P = a.P, nh = n1 / 2 + 1, half = n1 / 2;
   const int tid = threadIdx.x, nthr = LF > 0 ? 256 : (int)blockDim.x;
+  const RowLayout L = row_layout(MODE, n1, P, nthr, (int)sizeof(T));
   const int T8 = (n1 + kE - 1) / kE;          // threads per sequence
-  const int G = nthr / T8;                     // sequences per block pass
+  const int G = L.G;                           // sequences per batch
   const int grp = tid / T8, t = tid - grp * T8;
   const bool wsync = T8 <= 32 && (32 % T8) == 0;
-  const int pitch = rpitch(n1);
+  // fixed lengths: unpadded rows with the XOR swizzle; otherwise one spare slot per 8
+  const int pitch = LF > 0 ? LF : rpitch(n1);
   C* z = reinterpret_cast<C*>(smraw) + (size_t)grp * pitch;
+  auto zi = [](int e) { return LF > 0 ? rswz(e) : rpad(e); };
   const int nseq = a.nrows / 2;
+  const int nbatch = (nseq + G - 1) / G;
   const FftPlan plan = a.plan;
-  for (int s0 = blockIdx.x * G; s0 < nseq; s0 += gridDim.x * G) {
-    const int s = s0 + grp;
+  // fixed lengths, C2R: a batch's real output rows are assembled in its staging
+  // buffer and written by one bulk copy (FP64 accumulation keeps per-element
+  // updates).  R2C measured faster with direct stores (0.104 vs 0.112 ms at 256^3).
+  const bool bulk = LF > 0 && MODE == ROW_C2R && a.acc64 == nullptr && (L.outbytes & 15) == 0;
+  int buf = 0;
+  if ((int)blockIdx.x < nbatch) row_stage<T, MODE>(a, L, smraw, blockIdx.x, 0);
+  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
+    cp_async_wait_all();
+    if (bulk && tid == 0) bulk_wait_read_all();  // staging buffer buf ^ 1 is free again
+    __syncthreads();
+    if (b + (int)gridDim.x < nbatch) row_stage<T, MODE>(a, L, smraw, b + gridDim.x, buf ^ 1);
+    unsigned char* stg = smraw + L.zbytes + (size_t)buf * L.stage;
+    const size_t nr = min((size_t)2 * G, (size_t)a.nrows - 2 * (size_t)b * G);
+    const int s = b * G + grp;
     const bool act = grp < G && s < nseq;
     const size_t r0 = 2 * (size_t)s, r1 = r0 + 1;
     if (MODE == ROW_C2R) {
       if (act) {
-        const C* A = a.spec_in + r0 * P;
-        const C* B = a.spec_in + r1 * P;
-#pragma unroll 4
-        for (int k = t; k < n1; k += T8) {
-          const int kk = (k <= half) ? k : n1 - k;
-          C va = A[kk], vb = B[kk];
-          if (kk == 0 || kk == half) { va.y = 0; vb.y = 0; }
-          C w;
-          if (k <= half) { w.x = va.x - vb.y; w.y = va.y + vb.x; }
-          else { w.x = va.x + vb.y; w.y = vb.x - va.y; }
-          z[rpad(k)] = w;
+        const C* A = reinterpret_cast<const C*>(stg + (size_t)(2 * grp) * L.rowbytes);
+        const C* B = reinterpret_cast<const C*>(stg + (size_t)(2 * grp + 1) * L.rowbytes);
+        // Z[k] and its mirror Z[N1-k] from one read of A[k], B[k]
+#pragma unroll 2
+        for (int k = t; k <= half; k += T8) {
+          C va = A[k], vb = B[k];
+          const bool edge = (k == 0 || k == half);
+          if (edge) { va.y = 0; vb.y = 0; }
+          z[zi(k)] = cmk<C>(va.x - vb.y, va.y + vb.x);
+          if (!edge) z[zi(n1 - k)] = cmk<C>(va.x + vb.y, vb.x - va.y);
         }
       }
       group_sync(wsync);
       if constexpr (LF > 0) {
-        fft_fixed<LF, true, false, LF + LF / 8 + 1, 1, 3>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+        fft_fixed<LF, true, false, LF, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
       } else {
         fft_smem<true, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                               tid, nthr);
       }
+      if (bulk) {
+        __syncthreads();  // every group is done with the staged input
+        if (act) {
+          T* o = reinterpret_cast<T*>(stg) + (size_t)(2 * grp) * n1;
+          for (int x = t; x < n1; x += T8) {
+            const C w = z[zi(x)];
+            o[x] = w.x;
+            o[n1 + x] = w.y;
+          }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          bulk_s2g(a.real_out + 2 * (size_t)b * G * n1, stg, (unsigned)(nr * L.outbytes));
+          bulk_commit();
+        }
+        continue;
+      }
       group_sync(wsync);
       if (act) {
         for (int x = t; x < n1; x += T8) {
-          const C w = z[rpad(x)];
+          const C w = z[zi(x)];
           if (a.real_out) {
             a.real_out[r0 * n1 + x] = w.x;
             a.real_out[r1 * n1 + x] = w.y;
@@ -95,30 +180,55 @@ __global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
       }
     } else {
       if (act) {
-        const T* ra = a.real_in + r0 * n1;
-        const T* rb = a.real_in + r1 * n1;
+        const T* ra = reinterpret_cast<const T*>(stg + (size_t)(2 * grp) * L.rowbytes);
+        const T* rb = reinterpret_cast<const T*>(stg + (size_t)(2 * grp + 1) * L.rowbytes);
 #pragma unroll 4
         for (int x = t; x < n1; x += T8) {
           C w;
           w.x = ra[x];
           w.y = rb[x];
-          z[rpad(x)] = w;
+          z[zi(x)] = w;
         }
       }
       group_sync(wsync);
       if constexpr (LF > 0) {
-        fft_fixed<LF, false, false, LF + LF / 8 + 1, 1, 3>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+        fft_fixed<LF, false, false, LF, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
       } else {
         fft_smem<false, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
-                              tid, nthr);
+                               tid, nthr);
+      }
+      if (bulk) {
+        __syncthreads();  // every group is done with the staged input
+        if (act) {
+          C* A = reinterpret_cast<C*>(stg) + (size_t)(2 * grp) * P;
+          C* B = A + P;
+          for (int k = t; k < P; k += T8) {
+            C va = cmk<C>(0, 0), vb = cmk<C>(0, 0);
+            if (k < nh) {
+              const C zk = z[zi(k)];
+              const C zn = z[zi(k == 0 ? 0 : n1 - k)];
+              va = cmk<C>(T(0.5) * (zk.x + zn.x), T(0.5) * (zk.y - zn.y));
+              vb = cmk<C>(T(0.5) * (zk.y + zn.y), T(0.5) * (zn.x - zk.x));
+            }
+            A[k] = va;
+            B[k] = vb;
+          }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          bulk_s2g(a.spec_out + 2 * (size_t)b * G * P, stg, (unsigned)(nr * L.outbytes));
+          bulk_commit();
+        }
+        continue;
       }
       group_sync(wsync);
       if (act) {
         C* A = a.spec_out + r0 * P;
         C* B = a.spec_out + r1 * P;
         for (int k = t; k < nh; k += T8) {
-          const C zk = z[rpad(k)];
-          const C zn = z[rpad(k == 0 ? 0 : n1 - k)];
+          const C zk = z[zi(k)];
+          const C zn = z[zi(k == 0 ? 0 : n1 - k)];
           C va, vb;
           va.x = T(0.5) * (zk.x + zn.x);
           va.y = T(0.5) * (zk.y - zn.y);
@@ -129,8 +239,9 @@ __global__ void __launch_bounds__(256, 3) k_row(const RowArgs<T> a) {
         }
       }
     }
-    group_sync(wsync);
   }
+  cp_async_wait_all();
+  if (bulk && tid == 0) bulk_wait_all();
 }
 
 }  // namespace hs
