@@ -842,6 +842,8 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   nzc = (c->n3 + c->zc - 1) / c->zc;
   c->grid_m = dim3(ytiles, nzc);
   // measured on GB300 at 256^3: narrow tiles in small blocks overlap best
+  // (compile-time y/z kernels: 256 threads 0.096 / 0.218 ms, 768 threads
+  // 0.115 / 0.235 ms per y / z+Green pass)
   c->ct = c->f64 ? 4 : 8;
   if (o.col_tile > 0) {
     if (o.col_tile != (c->f64 ? 8 : 16) && o.col_tile != (c->f64 ? 4 : 8)) {

@@ -161,27 +161,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   const C* __restrict__ tw = a.tw;
   constexpr int W = 3 * CT;
   const int ccols = min(CT, a.P - x0);
-  if constexpr (LF > 0) {
-    // first stage straight from global memory, last stage straight back
-    ColIO<C> io;
-    io.cstride = cstride;
-    io.rstride = rstride;
-    io.ccols = ccols;
-    io.ncol = ncol;
-    io.gout = a.buf + base;
-    if (MODE == COL_Z_GREEN) {
-      io.gin = a.buf + base;
-      fft_col_fixed<LF, W, CT, false, true, false>(sm, io, tw, tid, nthr);
-      col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
-      __syncthreads();
-      fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, nthr);
-    } else {
-      io.gin = src + base;
-      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, true, true>(sm, io, tw, tid, nthr);
-    }
-    return;
-  }
-  // tile load: 16-byte asynchronous copies; columns past the row pitch are zero
+  // tile load: 16-byte asynchronous copies of the whole tile (every load in
+  // flight at once); columns past the row pitch are zero
   constexpr int EPC = 16 / (int)sizeof(C);  // complex values per 16-byte chunk
   constexpr int CPR = CT / EPC;             // chunks per (row, component)
   for (int i = tid; i < L * 3 * CPR; i += nthr) {
@@ -197,6 +178,25 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
+  if constexpr (LF > 0) {
+    // compile-time plan; the last stage writes straight to global memory
+    ColIO<C> io;
+    io.gin = nullptr;
+    io.gout = a.buf + base;
+    io.cstride = cstride;
+    io.rstride = rstride;
+    io.ccols = ccols;
+    io.ncol = ncol;
+    if (MODE == COL_Z_GREEN) {
+      fft_col_fixed<LF, W, CT, false, false, false>(sm, io, tw, tid, nthr);
+      col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+      __syncthreads();
+      fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, nthr);
+    } else {
+      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, false, true>(sm, io, tw, tid, nthr);
+    }
+    return;
+  }
   if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
     HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
   } else {
