@@ -176,6 +176,14 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
     }
   }
   cp_async_commit();
+  if (MODE == COL_Z_GREEN) {
+    // the Green step reads the state tile after the forward transform: start
+    // moving it into L2 now (one prefetch per 64-byte row segment)
+    for (int i = tid; i < L * 3; i += nthr) {
+      const int e = i / 3, c = i - 3 * e;
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
   if constexpr (LF > 0) {

@@ -46,10 +46,10 @@ static cudaError_t march_real(const MarchArgs<T>& a, bool iso, int ty, int mode,
   }
 }
 
-template <int TY, class MATP, int MODE>
+template <int TY, class MATP, int MODE, int N1 = 0>
 static cudaError_t stencil_one(const MarchArgs<float>& a, const MATP& m, dim3 g, int nthr, size_t smem,
                                cudaStream_t s) {
-  auto k = k_stencil<TY, MATP, MODE>;
+  auto k = k_stencil<TY, MATP, MODE, N1>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<g, nthr, smem, s>>>(a, m);
@@ -61,10 +61,18 @@ static cudaError_t stencil_ty(const MarchArgs<float>& a, bool iso, int mode, dim
                               cudaStream_t s) {
   if (iso) {
     MatIsoP m{a.mat};
+    if constexpr (TY == 4) {
+      if (mode == MODE_FORCE && a.n1 == 256 && nthr == 256)
+        return stencil_one<TY, MatIsoP, MODE_FORCE, 256>(a, m, g, nthr, smem, s);
+    }
     if (mode == MODE_FORCE) return stencil_one<TY, MatIsoP, MODE_FORCE>(a, m, g, nthr, smem, s);
     return stencil_one<TY, MatIsoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
   }
   MatAnisoP m{a.mat};
+  if constexpr (TY == 4) {
+    if (mode == MODE_FORCE && a.n1 == 256 && nthr == 256)
+      return stencil_one<TY, MatAnisoP, MODE_FORCE, 256>(a, m, g, nthr, smem, s);
+  }
   if (mode == MODE_FORCE) return stencil_one<TY, MatAnisoP, MODE_FORCE>(a, m, g, nthr, smem, s);
   return stencil_one<TY, MatAnisoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
 }

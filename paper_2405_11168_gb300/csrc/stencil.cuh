@@ -70,12 +70,12 @@ struct MatAnisoP {
 // of output plane ps into buffer ib (ps < 0: none).  Warp w copies rows w,
 // w + nwarps, ...; its lanes copy the 16-byte chunks of a row.  Ends with a
 // commit of the copy group.
-template <int TY>
+template <int TY, int N1>
 __device__ __forceinline__ void stencil_prefetch(const MarchArgs<float>& a, const MarchLayout& lay,
                                                  unsigned char* smraw, int y0, int pu, int slot, int ib, int ps,
                                                  bool want_ids) {
   constexpr int NR = TY + 2;
-  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const int n1 = N1 > 0 ? N1 : a.n1, n2 = a.n2, n3 = a.n3;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const size_t rplane = (size_t)n2 * n1, rcomp = (size_t)n3 * rplane;
   const int gz = pu < 0 ? pu + n3 : (pu >= n3 ? pu - n3 : pu);
@@ -132,12 +132,14 @@ __device__ __forceinline__ void stencil_prefetch(const MarchArgs<float>& a, cons
   cp_async_commit();
 }
 
-template <int TY, class MATP, int MODE>
+// N1 > 0: the x extent is a compile-time constant (hot sizes), so shared
+// memory row offsets become immediates; N1 = 0: taken at run time.
+template <int TY, class MATP, int MODE, int N1 = 0>
 __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const MATP mat) {
   constexpr int NR = TY + 2;
   if (a.skip_if_done && a.st->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const int n1 = N1 > 0 ? N1 : a.n1, n2 = a.n2, n3 = a.n3;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int y0 = blockIdx.x * TY;
   const int z0 = blockIdx.y * a.zc;
@@ -147,6 +149,8 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
   const bool has_src = (a.src != nullptr);
 
   const MarchLayout lay = march_layout(n1, 0, nthr, TY, MODE, true, has_src, 4);
+  const int n1i = N1 > 0 ? ((N1 + 7) & ~7) : lay.n1i;
+  const int n1s = N1 > 0 ? ((N1 + 3) & ~3) : lay.n1s;
   float* rring = reinterpret_cast<float*>(smraw + lay.ring);            // [3][3*NR][n1]
   uint16_t* sids = reinterpret_cast<uint16_t*>(smraw + lay.ids);        // [2][TY+1][n1i]
   float* ssrc = reinterpret_cast<float*>(smraw + lay.src);              // [2][3*TY][n1s]
@@ -175,8 +179,8 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
   const bool recv_edge = xact && !recv_shfl;
   const int src_warp = ((x + 1) % n1) >> 5;
 
-  stencil_prefetch<TY>(a, lay, smraw, y0, z0 - 1, 0, 0, -1, false);
-  stencil_prefetch<TY>(a, lay, smraw, y0, z0, 1, 0, -1, true);
+  stencil_prefetch<TY, N1>(a, lay, smraw, y0, z0 - 1, 0, 0, -1, false);
+  stencil_prefetch<TY, N1>(a, lay, smraw, y0, z0, 1, 0, -1, true);
 
   const int pend = (MODE == MODE_FORCE) ? z0 + zc : z0 + zc - 1;
   for (int p = z0; p <= pend; ++p) {
@@ -184,10 +188,10 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
     cp_async_wait_all();
     __syncthreads();
     const int sc = (p - z0 + 1) % 3, sp = (p - z0) % 3;
-    if (p < pend) stencil_prefetch<TY>(a, lay, smraw, y0, p + 1, (p - z0 + 2) % 3, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
+    if (p < pend) stencil_prefetch<TY, N1>(a, lay, smraw, y0, p + 1, (p - z0 + 2) % 3, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
     const int pz = p % n3;
     const bool own_plane = p < z0 + zc;
-    const uint16_t* idrow = sids + (size_t)ib * (TY + 1) * lay.n1i;
+    const uint16_t* idrow = sids + (size_t)ib * (TY + 1) * n1i;
     const float* rc = rring + (size_t)sc * 3 * NR * n1;  // corner plane p
     const float* rp = rring + (size_t)sp * 3 * NR * n1;  // corner plane p-1
 
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
         un[1][0][c] = rc[(c * NR + jj) * n1 + xmr];
         un[1][1][c] = rp[(c * NR + jj) * n1 + xmr];
       }
-      const int ph = idrow[(jj - 1) * lay.n1i + xr];
+      const int ph = idrow[(jj - 1) * n1i + xr];
       // T1 corner / mirror pairs: A = (000, 111), B = (011, 100), C = (110, 001), D = (101, 010)
       // with offset index [ox][oy][oz], 1 = coordinate - 1
       float2 g[3][3];  // g[i][j]: lane x = 2 D^T1_i u_j, lane y = -2 D^T2_i u_j
@@ -339,13 +343,13 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
     if (p > z0) {
       // corner plane p-1 is complete: undo the factor 4 of the accumulation
       const int zp = (p - 1) % n3;
-      const float* sr = ssrc + (size_t)ib * 3 * TY * lay.n1s;
+      const float* sr = ssrc + (size_t)ib * 3 * TY * n1s;
 #pragma unroll
       for (int r = 0; r < TY; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           float f = 0.25f * Fp[r][c];
-          if (has_src && xact) f += sr[(c * TY + r) * lay.n1s + x];
+          if (has_src && xact) f += sr[(c * TY + r) * n1s + x];
           Fp[r][c] = f;
         }
       if (xact) {
