@@ -104,7 +104,7 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
                     const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Solve for one applied macroscopic strain (Algorithm 1 under strain control).
- *  E          host, 6 tensor components in Voigt order; must not be all zero.
+ *  E          host, 6 tensor components in Voigt order; all zero only with an eigenstrain set.
  *  tol        stop at the first evaluation with err < tol (tol = 0: run max_iter evaluations).
  *  max_iter   maximum number of residual evaluations (>= 1).  The iteration count is the
  *             number of residual evaluations: a homogeneous medium converges in 1.
@@ -117,6 +117,31 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
  * error. */
 hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps_out,
                    void* sig_out, double sig_eff[6], int* iters, double* final_err);
+
+/* Solve under an applied macroscopic stress (Section 2.5, Eqs. Grand_Elast_energy and
+ * equi_epsilon_bar; Algorithm 1 step 6).  The macroscopic strain starts at
+ * E = (lambda0)^-1 : sigma^a and, after every evaluation that does not stop, moves to
+ * (lambda0)^-1 : {sigma^a + (lambda0 - <lambda>) : E - <lambda : deps> + <lambda : eps0>},
+ * evaluated in the equivalent form E + (lambda0)^-1 : (sigma^a - <sigma>).
+ *  S          host, 6: applied stress sigma^a in Voigt order (tensor components); all zero
+ *             only with an eigenstrain set.
+ *  E_out      host, 6 or NULL: the macroscopic strain of the last evaluation (tensor components).
+ *  Other arguments, outputs and return values as for hs_solve.
+ * Stopping: HS_FP64 and HS_FP32 stop on err < tol, as Algorithm 1 does (E is updated at
+ * every evaluation).  HS_FP32_REFINED updates E after every FP64 residual sweep and stops
+ * when err < tol and ||sigma^a - <sigma>||_F < tol * max(||sigma^a||_F, ||<sigma>||_F).
+ * The update converges at the rate set by lambda0 against the effective stiffness, so
+ * references far from it (very stiff inclusions with the Section 3.4 rule) need many
+ * evaluations. */
+hs_status hs_solve_stress(hs_ctx* c, const double S[6], double tol, int max_iter, void* eps_out,
+                          void* sig_out, double sig_eff[6], double E_out[6], int* iters, double* final_err);
+
+/* Per-phase eigenstrain eps0 (Eq. linear_elasticity: sigma = lambda(r) : (eps(r) - eps0(r))).
+ *  eps0       host, nphase x 6 tensor components in Voigt order, copied; NULL removes it.
+ * Applies to every later hs_solve / hs_solve_stress of this context.  Stress outputs and
+ * <sigma> include -lambda : eps0; the strain output is the total strain E + deps.
+ * Errors: HS_ERR_INVALID_ARG (non-finite values), HS_ERR_CUDA. */
+hs_status hs_set_eigenstrain(hs_ctx* c, const double* eps0);
 
 /* Error after each residual evaluation of the last hs_solve (HS_FP32_REFINED: of each FP64
  * residual sweep).  Writes min(n, available) values; *n_written gets the count. */

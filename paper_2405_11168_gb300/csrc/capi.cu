@@ -178,7 +178,7 @@ bool cholesky_pd(const double* A) {
 }
 
 struct Layout {
-  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, u64, rsrc, total;
+  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, u64, rsrc, total;
 };
 
 }  // namespace
@@ -210,6 +210,12 @@ struct hs_ctx {
   double* hist;
   double* u64;
   float* rsrc;
+  double* macro;   // device [sigma^a (6), S0 (36)] of the applied-stress loop
+  float* sig0f;    // device lambda(p) : eps0(p), Voigt, per phase (eigenstrain)
+  double* sig0d;
+  bool has_eigen = false;
+  bool dev_macro = false;    // plain modes under applied stress: E lives in the device status
+  double Einit[6] = {0, 0, 0, 0, 0, 0};
   FftPlan plan[3];
   int ty, zc, nthr_m;
   dim3 grid_m;
@@ -327,6 +333,9 @@ Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
   L.partials = off; off += align256(max_blocks * hs::NRED * 8);
   L.status = off; off += align256(sizeof(DevStatus));
   L.hist = off; off += align256((size_t)kHistCap * 8);
+  L.macro = off; off += align256(42 * 8);
+  L.sig0f = off; off += align256((size_t)nphase * 6 * 4);
+  L.sig0d = off; off += align256((size_t)nphase * 6 * 8);
   L.u64 = off;
   L.rsrc = off;
   if (prec == HS_FP32_REFINED) {
@@ -339,6 +348,10 @@ Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
 
 template <typename T> void fill_march_common(hs_ctx* c, hs::MarchArgs<T>& a) {
   memset(&a, 0, sizeof(a));
+  // full problem: eigenstrain and (plain modes) the device copy of E; the
+  // refined path's correction solves clear both
+  a.Edev = c->dev_macro ? &c->st->E[0] : nullptr;
+  a.sig0 = c->has_eigen ? (sizeof(T) == 8 ? (const T*)(const void*)c->sig0d : (const T*)(const void*)c->sig0f) : nullptr;
   a.ids = c->ids;
   a.mat = (const T*)(sizeof(T) == 8 && !c->f64 ? (void*)c->matd : c->matk);
   a.tw1 = (const typename hs::cplx_t<T>::type*)c->twk[0];
@@ -381,6 +394,10 @@ template <typename T> hs_status launch_force(hs_ctx* c, const double E[6], int i
   a.out = (typename hs::cplx_t<T>::type*)c->B[in ^ 1];
   for (int i = 0; i < 6; ++i) a.E[i] = (T)E[i];
   a.src = src;
+  if (src != nullptr) {
+    a.sig0 = nullptr;
+    a.Edev = nullptr;
+  }
   a.skip_if_done = 1;
   const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, hs::MODE_FORCE, false, src != nullptr);
   LaunchScope ls(c, HS_K_XPASS);
@@ -422,6 +439,10 @@ template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], con
   a.ureal = (const T*)c->B[1];
   for (int i = 0; i < 6; ++i) a.E[i] = (T)E[i];
   a.src = src;
+  if (src != nullptr) {  // correction equation K du = -r: linear, no eigenstrain, macro strain 0
+    a.sig0 = nullptr;
+    a.Edev = nullptr;
+  }
   a.fout = c->F;
   a.fout_f32 = 0;
   a.eps_out = eps;
@@ -507,6 +528,8 @@ hs_status reset_status(hs_ctx* c, double tol, int max_iter, double denom) {
   h.tol = tol;
   h.denom = denom;
   h.nvox = (double)c->N;
+  h.macro = c->dev_macro ? c->macro : nullptr;
+  for (int i = 0; i < 6; ++i) h.E[i] = c->Einit[i];
   HS_CU(c, cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   return HS_OK;
 }
@@ -561,7 +584,7 @@ hs_status status_code(const DevStatus& h) {
 
 template <typename T>
 hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps, void* sig,
-                      double sig_eff[6], int* iters, double* final_err) {
+                      double sig_eff[6], int* iters, double* final_err, double* E_final) {
   hs_status s = reset_status(c, tol, max_iter, 0.0);
   if (s != HS_OK) return s;
   c->cur = 0;
@@ -591,6 +614,7 @@ hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, vo
   c->hist_host.resize(n);
   if (n) HS_CU(c, cudaMemcpy(c->hist_host.data(), c->hist, n * sizeof(double), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 6; ++i) sig_eff[i] = h.sig_mean[i];
+  if (E_final) for (int i = 0; i < 6; ++i) E_final[i] = c->dev_macro ? h.E[i] : E[i];
   if (iters) *iters = h.evals;
   if (final_err) *final_err = h.err;
   return status_code(h);
@@ -630,8 +654,23 @@ hs_status launch_emit(hs_ctx* c, int in) {
   return HS_OK;
 }
 
-hs_status solve_refined(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps, void* sig,
-                        double sig_eff[6], int* iters, double* final_err) {
+// Frobenius norm of a Voigt-ordered symmetric tensor (shear entries counted twice)
+double frob(const double v[6]) {
+  double s = 0;
+  for (int i = 0; i < 6; ++i) s += (i < 3 ? 1.0 : 2.0) * v[i] * v[i];
+  return std::sqrt(s);
+}
+
+// Sa != nullptr: applied-stress control.  The FP64 sweeps use the current
+// macroscopic strain; after a sweep that does not stop, E <- E + S0 (sigma^a -
+// <sigma>) (Algorithm 1 step 6, regrouped), and stopping also needs
+// ||sigma^a - <sigma>|| < tol max(||sigma^a||, ||<sigma>||): the correction
+// solves restore equilibrium for a given E long before E settles.
+hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter, void* eps, void* sig,
+                        double sig_eff[6], int* iters, double* final_err, const double* Sa, const double* S0,
+                        double* E_final) {
+  double E[6];
+  for (int i = 0; i < 6; ++i) E[i] = E0[i];
   HS_CU(c, cudaMemsetAsync(c->u64, 0, 3 * c->N * sizeof(double), c->stream));
   c->hist_host.clear();
   int total = 0;
@@ -648,8 +687,22 @@ hs_status solve_refined(hs_ctx* c, const double E[6], double tol, int max_iter, 
     total += 1;
     c->hist_host.push_back(h64.err);
     if (!(h64.err == h64.err) || h64.err > 1e300) { result = HS_DIVERGED; break; }
-    if (h64.err < tol) { result = HS_OK; break; }
+    bool stress_ok = true;
+    if (Sa != nullptr) {
+      double d[6];
+      for (int i = 0; i < 6; ++i) d[i] = Sa[i] - h64.sig_mean[i];
+      const double den = std::max({frob(Sa), frob(h64.sig_mean), 1e-300});
+      stress_ok = frob(d) < tol * den;
+    }
+    if (h64.err < tol && stress_ok) { result = HS_OK; break; }
     if (total >= max_iter) { result = HS_NOT_CONVERGED; break; }
+    if (Sa != nullptr) {
+      for (int i = 0; i < 6; ++i) {
+        double acc = 0;
+        for (int j = 0; j < 6; ++j) acc += S0[i * 6 + j] * (Sa[j] - h64.sig_mean[j]);
+        E[i] += acc;
+      }
+    }
     // correction solve: K du = -r in FP32, source r = rsrc, macro strain 0
     const int budget = std::min(std::max(1, c->opt.inner_max), max_iter - total);
     s = reset_status(c, c->opt.inner_ratio * h64.err, budget, h64.sig_norm);
@@ -674,9 +727,38 @@ hs_status solve_refined(hs_ctx* c, const double E[6], double tol, int max_iter, 
   }
   HS_CU(c, cudaStreamSynchronize(c->stream));
   for (int i = 0; i < 6; ++i) sig_eff[i] = h64.sig_mean[i];
+  if (E_final) for (int i = 0; i < 6; ++i) E_final[i] = E[i];
   if (iters) *iters = total;
   if (final_err) *final_err = h64.err;
   return result;
+}
+
+// 6x6 inverse by Gauss-Jordan elimination with partial pivoting; false if singular
+bool inv6(const double A[36], double X[36]) {
+  double M[6][12];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 12; ++j) M[i][j] = j < 6 ? A[i * 6 + j] : (j - 6 == i ? 1.0 : 0.0);
+  double scale = 0;
+  for (int i = 0; i < 36; ++i) scale = std::max(scale, std::fabs(A[i]));
+  for (int col = 0; col < 6; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 6; ++r)
+      if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+    if (!(std::fabs(M[piv][col]) > 1e-14 * scale)) return false;
+    if (piv != col)
+      for (int j = 0; j < 12; ++j) std::swap(M[piv][j], M[col][j]);
+    const double d = M[col][col];
+    for (int j = 0; j < 12; ++j) M[col][j] /= d;
+    for (int r = 0; r < 6; ++r) {
+      if (r == col) continue;
+      const double f = M[r][col];
+      if (f != 0)
+        for (int j = 0; j < 12; ++j) M[r][j] -= f * M[col][j];
+    }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) X[i * 6 + j] = M[i][j + 6];
+  return true;
 }
 
 }  // namespace
@@ -824,6 +906,9 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   c->partials = (double*)(c->ws + c->lay.partials);
   c->st = (DevStatus*)(c->ws + c->lay.status);
   c->hist = (double*)(c->ws + c->lay.hist);
+  c->macro = (double*)(c->ws + c->lay.macro);
+  c->sig0f = (float*)(c->ws + c->lay.sig0f);
+  c->sig0d = (double*)(c->ws + c->lay.sig0d);
   c->u64 = (o.precision == HS_FP32_REFINED) ? (double*)(c->ws + c->lay.u64) : nullptr;
   c->rsrc = (o.precision == HS_FP32_REFINED) ? (float*)(c->ws + c->lay.rsrc) : nullptr;
   c->warm = false;
@@ -1036,7 +1121,8 @@ hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void*
     if (!std::isfinite(E[i])) return fail(c, HS_ERR_INVALID_ARG, "non-finite E");
     en += E[i] * E[i];
   }
-  if (en == 0) return fail(c, HS_ERR_INVALID_ARG, "E = 0 (the error norm would divide by <sigma> = 0)");
+  if (en == 0 && !c->has_eigen)
+    return fail(c, HS_ERR_INVALID_ARG, "E = 0 without eigenstrain (the error norm would divide by <sigma> = 0)");
   if ((eps_out == nullptr) != (sig_out == nullptr)) return fail(c, HS_ERR_INVALID_ARG, "give both or neither field output");
   if (eps_out) {
     cudaPointerAttributes a1, a2;
@@ -1047,9 +1133,104 @@ hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void*
       return fail(c, HS_ERR_INVALID_ARG, "field outputs must be device pointers");
   }
   c->last_err.clear();
-  if (c->prec == HS_FP32_REFINED) return solve_refined(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err);
-  if (c->f64) return solve_plain<double>(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err);
-  return solve_plain<float>(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err);
+  c->dev_macro = false;
+  for (int i = 0; i < 6; ++i) c->Einit[i] = 0;
+  if (c->prec == HS_FP32_REFINED)
+    return solve_refined(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err, nullptr, nullptr, nullptr);
+  if (c->f64) return solve_plain<double>(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err, nullptr);
+  return solve_plain<float>(c, E, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err, nullptr);
+}
+
+hs_status hs_solve_stress(hs_ctx* c, const double S[6], double tol, int max_iter, void* eps_out, void* sig_out,
+                          double sig_eff[6], double E_out[6], int* iters, double* final_err) {
+  if (!c || !S || !sig_eff) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (!(tol >= 0) || max_iter < 1) return fail(c, HS_ERR_INVALID_ARG, "bad tol or max_iter");
+  double sn = 0;
+  for (int i = 0; i < 6; ++i) {
+    if (!std::isfinite(S[i])) return fail(c, HS_ERR_INVALID_ARG, "non-finite applied stress");
+    sn += S[i] * S[i];
+  }
+  if (sn == 0 && !c->has_eigen)
+    return fail(c, HS_ERR_INVALID_ARG, "applied stress 0 without eigenstrain: the solution is u = 0, E = 0");
+  if ((eps_out == nullptr) != (sig_out == nullptr)) return fail(c, HS_ERR_INVALID_ARG, "give both or neither field output");
+  if (eps_out) {
+    cudaPointerAttributes a1, a2;
+    cudaError_t e1 = cudaPointerGetAttributes(&a1, eps_out), e2 = cudaPointerGetAttributes(&a2, sig_out);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) cudaGetLastError();
+    if (e1 != cudaSuccess || e2 != cudaSuccess || (a1.type != cudaMemoryTypeDevice && a1.type != cudaMemoryTypeManaged) ||
+        (a2.type != cudaMemoryTypeDevice && a2.type != cudaMemoryTypeManaged))
+      return fail(c, HS_ERR_INVALID_ARG, "field outputs must be device pointers");
+  }
+  // S0: Voigt stress -> tensor strain components of (lambda0)^-1 : sigma
+  double Cinv[36], S0[36];
+  if (!inv6(c->C0, Cinv)) return fail(c, HS_ERR_INVALID_ARG, "reference medium is singular");
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) S0[i * 6 + j] = (i < 3 ? 1.0 : 0.5) * Cinv[i * 6 + j];
+  // initial guess E = (lambda0)^-1 : sigma^a (Algorithm 1)
+  double E0[6];
+  for (int i = 0; i < 6; ++i) {
+    double acc = 0;
+    for (int j = 0; j < 6; ++j) acc += S0[i * 6 + j] * S[j];
+    E0[i] = acc;
+  }
+  c->last_err.clear();
+  double Efin[6];
+  hs_status st;
+  if (c->prec == HS_FP32_REFINED) {
+    c->dev_macro = false;
+    for (int i = 0; i < 6; ++i) c->Einit[i] = 0;
+    st = solve_refined(c, E0, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err, S, S0, Efin);
+  } else {
+    double host_macro[42];
+    for (int i = 0; i < 6; ++i) host_macro[i] = S[i];
+    for (int i = 0; i < 36; ++i) host_macro[6 + i] = S0[i];
+    cudaError_t e = cudaMemcpyAsync(c->macro, host_macro, sizeof(host_macro), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "applied stress upload");
+    c->dev_macro = true;
+    for (int i = 0; i < 6; ++i) c->Einit[i] = E0[i];
+    st = c->f64 ? solve_plain<double>(c, E0, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err, Efin)
+                : solve_plain<float>(c, E0, tol, max_iter, eps_out, sig_out, sig_eff, iters, final_err, Efin);
+    c->dev_macro = false;
+    for (int i = 0; i < 6; ++i) c->Einit[i] = 0;
+  }
+  if (st >= 0 && E_out)
+    for (int i = 0; i < 6; ++i) E_out[i] = Efin[i];
+  return st;
+}
+
+hs_status hs_set_eigenstrain(hs_ctx* c, const double* eps0) {
+  if (!c) return HS_ERR_INVALID_ARG;
+  if (eps0 == nullptr) {
+    c->has_eigen = false;
+    return HS_OK;
+  }
+  std::vector<double> s0d((size_t)c->nphase * 6);
+  std::vector<float> s0f((size_t)c->nphase * 6);
+  bool any = false;
+  for (int p = 0; p < c->nphase; ++p) {
+    const double* e = eps0 + (size_t)p * 6;
+    double eng[6];
+    for (int i = 0; i < 6; ++i) {
+      if (!std::isfinite(e[i])) return fail(c, HS_ERR_INVALID_ARG, "non-finite eigenstrain");
+      eng[i] = (i < 3 ? 1.0 : 2.0) * e[i];
+      any = any || e[i] != 0;
+    }
+    const double* C = c->table.data() + (size_t)p * 36;
+    for (int i = 0; i < 6; ++i) {
+      double acc = 0;
+      for (int j = 0; j < 6; ++j) acc += C[i * 6 + j] * eng[j];
+      s0d[(size_t)p * 6 + i] = acc;
+      s0f[(size_t)p * 6 + i] = (float)acc;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(c->sig0d, s0d.data(), s0d.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->sig0f, s0f.data(), s0f.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "eigenstrain upload");
+  c->has_eigen = any;
+  return HS_OK;
 }
 
 hs_status hs_err_history(const hs_ctx* c, double* out, int n, int* n_written) {

@@ -25,6 +25,14 @@ struct DevStatus {
   double err_min;
   double denom;     // > 0: use this instead of sig_norm (correction solves)
   double nvox;      // N
+  // Applied-stress control (Section 2.5, Algorithm 1 step 6): when macro is
+  // not null it points at [sigma^a (6, Voigt), S0 (6x6)], S0 mapping a Voigt
+  // stress to the tensor strain components of (lambda0)^-1 : sigma, and every
+  // evaluation that does not stop moves the macroscopic strain E (tensor
+  // components, read by the kernels of the next evaluation) by
+  // S0 (sigma^a - <sigma>).
+  const double* macro;
+  double E[6];
 };
 
 enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
@@ -139,6 +147,22 @@ __device__ inline void reduce_and_finalize(const double (&acc)[NRED], double* pa
       if (err < st->tol) st->done = DONE_CONVERGED;
       else if (err > 1e6 * st->err_min && k > 10) st->done = DONE_DIVERGED;
       else if (k + 1 >= st->max_iter) st->done = DONE_MAXITER;
+    }
+    if (st->macro != nullptr && st->done == DONE_RUNNING) {
+      // E <- (lambda0)^-1 : {sigma^a + (lambda0 - <lambda>) : E - <lambda : deps> + <lambda : eps0>}
+      //    = E + (lambda0)^-1 : (sigma^a - <sigma>)   (the same quantity, regrouped)
+      const double* Sa = st->macro;
+      const double* S0 = st->macro + 6;
+      double d[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) d[i] = Sa[i] - sm[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        double acc = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += S0[i * 6 + j] * d[j];
+        st->E[i] += acc;
+      }
     }
     st->counter = 0;
   }

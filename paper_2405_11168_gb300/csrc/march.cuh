@@ -52,7 +52,15 @@ template <typename T> struct MarchArgs {
   void* fout;            // REAL FORCE: real force [3][n3][n2][n1], float if fout_f32 else T
   int fout_f32;
   int skip_if_done;
+  const double* Edev;    // not null: the macroscopic strain is read here (applied-stress control)
+  const T* sig0;         // not null: lambda(ph) : eps0(ph) per phase, Voigt [nphase][6] (eigenstrain)
 };
+
+// Macroscopic strain of this evaluation: the kernel parameter, or the device
+// copy that the applied-stress loop updates.
+template <typename T> __device__ __forceinline__ T macro_E(const MarchArgs<T>& a, int i) {
+  return a.Edev != nullptr ? (T)a.Edev[i] : a.E[i];
+}
 
 // corner values u[ox][oy][oz][comp]; offset index 1 means coordinate - 1
 template <typename T>
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
   T facc = 0;
   T E[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) E[i] = a.E[i];
+  for (int i = 0; i < 6; ++i) E[i] = macro_E(a, i);
 
   const bool recv_shfl = (lane < 31) && (x + 1 < n1);
   const bool recv_edge = xact && !recv_shfl;
@@ -474,6 +482,14 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
         tetra_strains(u, E, e1, e2);
         mat.stress(ph, e1, s1);
         mat.stress(ph, e2, s2);
+        if (a.sig0 != nullptr) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            const T s0 = a.sig0[6 * ph + i];
+            s1[i] -= s0;
+            s2[i] -= s0;
+          }
+        }
         if (xact && own_plane) {
           const size_t o = (size_t)pz * rplane + (size_t)yv * n1 + x;
 #pragma unroll
@@ -500,6 +516,10 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
         T ev[6], sv[6];
         tetra_strain_fast(u, E, tt, ev);
         mat.stress(ph, ev, sv);
+        if (a.sig0 != nullptr) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) sv[i] -= a.sig0[6 * ph + i];
+        }
         if (!xact) {
 #pragma unroll
           for (int i = 0; i < 6; ++i) sv[i] = 0;

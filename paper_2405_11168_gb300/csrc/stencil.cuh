@@ -171,9 +171,11 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
 #pragma unroll
   for (int i = 0; i < 6; ++i) sacc[i] = make_float2(0.f, 0.f);
   float facc = 0.f;
-  // 1/2 and -1/2 undo the packing; the engineering macro strain is read
-  // from the kernel parameters where it is used
+  // 1/2 and -1/2 undo the packing
   const float2 hh = make_float2(0.5f, -0.5f);
+  float Em[6];  // engineering macro strain
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Em[i] = (i < 3 ? 1.f : 2.f) * macro_E(a, i);
 
   const bool recv_shfl = (lane < 31) && (x + 1 < n1);
   const bool recv_edge = xact && !recv_shfl;
@@ -243,13 +245,17 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a, const
         g[2][j] = p2add(mm, nn);
       }
       float2 e[6], s[6];
-      e[0] = p2fma(hh, g[0][0], p2dup(a.E[0]));
-      e[1] = p2fma(hh, g[1][1], p2dup(a.E[1]));
-      e[2] = p2fma(hh, g[2][2], p2dup(a.E[2]));
-      e[3] = p2fma(hh, p2add(g[1][2], g[2][1]), p2dup(2.f * a.E[3]));
-      e[4] = p2fma(hh, p2add(g[0][2], g[2][0]), p2dup(2.f * a.E[4]));
-      e[5] = p2fma(hh, p2add(g[0][1], g[1][0]), p2dup(2.f * a.E[5]));
+      e[0] = p2fma(hh, g[0][0], p2dup(Em[0]));
+      e[1] = p2fma(hh, g[1][1], p2dup(Em[1]));
+      e[2] = p2fma(hh, g[2][2], p2dup(Em[2]));
+      e[3] = p2fma(hh, p2add(g[1][2], g[2][1]), p2dup(Em[3]));
+      e[4] = p2fma(hh, p2add(g[0][2], g[2][0]), p2dup(Em[4]));
+      e[5] = p2fma(hh, p2add(g[0][1], g[1][0]), p2dup(Em[5]));
       mat.stress(ph, e, s);
+      if (a.sig0 != nullptr) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s[i] = p2sub(s[i], p2dup(a.sig0[6 * ph + i]));
+      }
       const int yv = y0 + jj - 1;
       if (MODE == MODE_FIELDS) {
         if (xact && own_plane) {

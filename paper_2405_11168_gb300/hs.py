@@ -37,6 +37,8 @@ EXPORTS = [
     "hs_workspace_size",
     "hs_create",
     "hs_solve",
+    "hs_solve_stress",
+    "hs_set_eigenstrain",
     "hs_err_history",
     "hs_get_state",
     "hs_set_state",
@@ -90,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.hs_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
                               dptr, ctypes.POINTER(hs_options), P, ctypes.c_size_t, P]
     lib.hs_solve.argtypes = [P, dptr, D, I, P, P, dptr, iptr, dptr]
+    lib.hs_solve_stress.argtypes = [P, dptr, D, I, P, P, dptr, dptr, iptr, dptr]
+    lib.hs_set_eigenstrain.argtypes = [P, dptr]
     lib.hs_err_history.argtypes = [P, dptr, I, iptr]
     lib.hs_get_state.argtypes = [P, P]
     lib.hs_set_state.argtypes = [P, P]
@@ -199,6 +203,38 @@ class Solver:
                               _dp(sig_eff), ctypes.byref(iters), ctypes.byref(err))
         _check(self.lib, s, self.ctx)
         return dict(status=s, iters=iters.value, err=err.value, sig_eff=sig_eff, eps=eps, sig=sig)
+
+    def _fields(self, fields):
+        torch = self.torch
+        if not fields:
+            return None, None
+        dt = torch.float32 if self.opt.out_f32 else torch.float64
+        shp = (6, self.grid[2], self.grid[1], self.grid[0])
+        return (torch.empty(shp, dtype=dt, device=self.workspace.device),
+                torch.empty(shp, dtype=dt, device=self.workspace.device))
+
+    def solve_stress(self, S, tol=1e-8, max_iter=1000, fields=True):
+        """Applied-stress solve; returns dict(status, iters, err, sig_eff, E, eps, sig)."""
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(6))
+        eps, sig = self._fields(fields)
+        sig_eff = np.zeros(6)
+        E = np.zeros(6)
+        iters = ctypes.c_int()
+        err = ctypes.c_double()
+        s = self.lib.hs_solve_stress(self.ctx, _dp(S), float(tol), int(max_iter),
+                                     ctypes.c_void_p(eps.data_ptr() if fields else 0),
+                                     ctypes.c_void_p(sig.data_ptr() if fields else 0),
+                                     _dp(sig_eff), _dp(E), ctypes.byref(iters), ctypes.byref(err))
+        _check(self.lib, s, self.ctx)
+        return dict(status=s, iters=iters.value, err=err.value, sig_eff=sig_eff, E=E, eps=eps, sig=sig)
+
+    def set_eigenstrain(self, eps0):
+        """Per-phase eigenstrain, (nphase, 6) tensor components in Voigt order; None removes it."""
+        if eps0 is None:
+            _check(self.lib, self.lib.hs_set_eigenstrain(self.ctx, None), self.ctx)
+            return
+        e = np.ascontiguousarray(np.asarray(eps0, dtype=np.float64).reshape(-1, 6))
+        _check(self.lib, self.lib.hs_set_eigenstrain(self.ctx, _dp(e)), self.ctx)
 
     def err_history(self, n=1 << 16):
         out = np.zeros(n)
