@@ -76,11 +76,25 @@ typedef struct {
   int col_tile;         /* y/z FFT tile width in complex columns: 0 = automatic; FP32 8 or 16, FP64 4 or 8 */
   int col_threads;      /* threads per y/z FFT block: 0 = automatic; a multiple of 32, at most 768 (FP32)
                            or 384 (FP64) */
+  int use_graphs;       /* 1 (default): after its first chunk, a solve replays its iteration chunks
+                           (check_every iterations) as one captured CUDA graph; 0: plain launches.
+                           Profiling (hs_profile_enable) always uses plain launches. */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
  * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0, col_tile 0, col_threads 0. */
 hs_status hs_default_options(hs_options* opt);
+
+/* Autotuner with a process-wide plan cache (no counterpart in the paper: it picks launch
+ * shapes, not numerics).  Times `iters` evaluations of each candidate tiling of the
+ * real-space and FFT passes (y tile 2/4/8 x z chunk, then the wider column tile) with
+ * CUDA events on `stream`, using the caller's workspace (hs_workspace_size bytes for
+ * `base`), and writes the fastest options to *best (*best_ms: ms per evaluation, or -1
+ * when the plan came from the cache).  Results do not depend on the tiling beyond
+ * rounding order.  Keyed by grid, precision and whether all phases are isotropic.
+ * Errors: as hs_create / hs_solve; HS_ERR_CUDA if no candidate ran. */
+hs_status hs_autotune(const int grid[3], const hs_material* m, const hs_options* base, void* workspace,
+                      size_t workspace_bytes, void* stream, int iters, hs_options* best, double* best_ms);
 
 /* Device workspace (bytes) that hs_create needs for this grid, precision and
  * number of phases.  The caller allocates it (e.g. as a PyTorch tensor) and

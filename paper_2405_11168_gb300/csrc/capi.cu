@@ -7,7 +7,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/hs.h"
@@ -214,6 +217,9 @@ struct hs_ctx {
   float* sig0f;    // device lambda(p) : eps0(p), Voigt, per phase (eigenstrain)
   double* sig0d;
   bool has_eigen = false;
+  // captured iteration chunks: [0] full problem, [1] correction solves (refined)
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int gchunks[2] = {0, 0};   // uncaptured chunks run so far (capture follows the first)
   bool dev_macro = false;    // plain modes under applied stress: E lives in the device status
   double Einit[6] = {0, 0, 0, 0, 0, 0};
   FftPlan plan[3];
@@ -350,7 +356,7 @@ template <typename T> void fill_march_common(hs_ctx* c, hs::MarchArgs<T>& a) {
   memset(&a, 0, sizeof(a));
   // full problem: eigenstrain and (plain modes) the device copy of E; the
   // refined path's correction solves clear both
-  a.Edev = c->dev_macro ? &c->st->E[0] : nullptr;
+  a.Edev = &c->st->E[0];
   a.sig0 = c->has_eigen ? (sizeof(T) == 8 ? (const T*)(const void*)c->sig0d : (const T*)(const void*)c->sig0f) : nullptr;
   a.ids = c->ids;
   a.mat = (const T*)(sizeof(T) == 8 && !c->f64 ? (void*)c->matd : c->matk);
@@ -520,7 +526,7 @@ template <typename T> hs_status launch_fields(hs_ctx* c, const double E[6], int 
   return HS_OK;
 }
 
-hs_status reset_status(hs_ctx* c, double tol, int max_iter, double denom) {
+hs_status reset_status(hs_ctx* c, double tol, int max_iter, double denom, const double* E = nullptr) {
   DevStatus h;
   memset(&h, 0, sizeof(h));
   h.max_iter = max_iter;
@@ -529,7 +535,7 @@ hs_status reset_status(hs_ctx* c, double tol, int max_iter, double denom) {
   h.denom = denom;
   h.nvox = (double)c->N;
   h.macro = c->dev_macro ? c->macro : nullptr;
-  for (int i = 0; i < 6; ++i) h.E[i] = c->Einit[i];
+  for (int i = 0; i < 6; ++i) h.E[i] = E ? E[i] : c->Einit[i];
   HS_CU(c, cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   return HS_OK;
 }
@@ -552,7 +558,18 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
   const int cur0 = c->cur;
   int cur = cur0;
   const int chunk = std::max(1, c->opt.check_every);
+  const bool graphs = c->opt.use_graphs && !c->prof && !c->xfuse;
+  const int gi = (src != nullptr) ? 1 : 0;
   for (;;) {
+    if (graphs && c->gexec[gi] != nullptr) {
+      HS_CU(c, cudaGraphLaunch(c->gexec[gi], c->stream));
+      hs_status s = read_status(c, hst);
+      if (s != HS_OK) return s;
+      if (hst->done) break;
+      continue;
+    }
+    const bool capture = graphs && c->gchunks[gi] >= 1;
+    if (capture) HS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < chunk; ++i) {
       if (c->xfuse) {
         hs_status s = launch_force<T>(c, E, cur, src);
@@ -565,9 +582,29 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
         if (s == HS_OK) s = launch_stencil<T>(c, E, src, hs::MODE_FORCE, nullptr, nullptr);
         if (s == HS_OK) s = launch_rows<T>(c, hs::ROW_R2C, nullptr, true);
         if (s == HS_OK) s = launch_cols<T>(c, 0);
-        if (s != HS_OK) return s;
+        if (s != HS_OK) {
+          if (capture) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(c->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+          }
+          return s;
+        }
       }
     }
+    if (capture) {
+      // the captured chunk has not run yet: instantiate it, keep it, and launch it
+      cudaGraph_t g = nullptr;
+      HS_CU(c, cudaStreamEndCapture(c->stream, &g));
+      cudaGraphExec_t ex = nullptr;
+      cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      c->gexec[gi] = ex;
+      HS_CU(c, cudaGraphLaunch(ex, c->stream));
+    }
+    ++c->gchunks[gi];
     hs_status s = read_status(c, hst);
     if (s != HS_OK) return s;
     if (hst->done) break;
@@ -585,7 +622,7 @@ hs_status status_code(const DevStatus& h) {
 template <typename T>
 hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps, void* sig,
                       double sig_eff[6], int* iters, double* final_err, double* E_final) {
-  hs_status s = reset_status(c, tol, max_iter, 0.0);
+  hs_status s = reset_status(c, tol, max_iter, 0.0, c->dev_macro ? nullptr : E);
   if (s != HS_OK) return s;
   c->cur = 0;
   if (c->warm) {
@@ -678,7 +715,7 @@ hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter,
   const double zeroE[6] = {0, 0, 0, 0, 0, 0};
   hs_status result = HS_NOT_CONVERGED;
   for (;;) {
-    hs_status s = reset_status(c, 0.0, 1 << 30, 0.0);
+    hs_status s = reset_status(c, 0.0, 1 << 30, 0.0, E);
     if (s != HS_OK) return s;
     s = launch_residual64(c, E, hs::MODE_FORCE, nullptr, nullptr);
     if (s != HS_OK) return s;
@@ -705,7 +742,7 @@ hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter,
     }
     // correction solve: K du = -r in FP32, source r = rsrc, macro strain 0
     const int budget = std::min(std::max(1, c->opt.inner_max), max_iter - total);
-    s = reset_status(c, c->opt.inner_ratio * h64.err, budget, h64.sig_norm);
+    s = reset_status(c, c->opt.inner_ratio * h64.err, budget, h64.sig_norm, zeroE);
     if (s != HS_OK) return s;
     HS_CU(c, cudaMemsetAsync(c->S, 0, cbuf_bytes(c), c->stream));
     HS_CU(c, cudaMemsetAsync(c->B[0], 0, cbuf_bytes(c), c->stream));
@@ -777,6 +814,7 @@ hs_status hs_default_options(hs_options* opt) {
   opt->xfuse = 0;
   opt->col_tile = 0;
   opt->col_threads = 0;
+  opt->use_graphs = 1;
   return HS_OK;
 }
 
@@ -803,7 +841,8 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED || o.check_every < 1 || o.inner_max < 1 ||
       !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0 ||
       !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
-      (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0)
+      (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0 ||
+      (o.use_graphs != 0 && o.use_graphs != 1))
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > 65536)
@@ -1199,8 +1238,18 @@ hs_status hs_solve_stress(hs_ctx* c, const double S[6], double tol, int max_iter
   return st;
 }
 
+// captured chunks hold kernel arguments: drop them when an argument changes
+static void drop_graphs(hs_ctx* c) {
+  for (int i = 0; i < 2; ++i) {
+    if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
+    c->gexec[i] = nullptr;
+    c->gchunks[i] = 0;
+  }
+}
+
 hs_status hs_set_eigenstrain(hs_ctx* c, const double* eps0) {
   if (!c) return HS_ERR_INVALID_ARG;
+  drop_graphs(c);
   if (eps0 == nullptr) {
     c->has_eigen = false;
     return HS_OK;
@@ -1262,6 +1311,129 @@ hs_status hs_set_state(hs_ctx* c, const void* uhat) {
   return HS_OK;
 }
 
+// --------------------------------------------------------------------------
+// Autotuner: time candidate tilings on the caller's workspace and keep the
+// fastest per (grid, precision, isotropy) in a process-wide plan cache.
+// --------------------------------------------------------------------------
+namespace {
+struct PlanKey {
+  int n1, n2, n3, prec, iso;
+  bool operator<(const PlanKey& o) const {
+    return std::tie(n1, n2, n3, prec, iso) < std::tie(o.n1, o.n2, o.n3, o.prec, o.iso);
+  }
+};
+std::mutex g_plan_mu;
+std::map<PlanKey, hs_options> g_plans;
+
+bool table_isotropic(const double* table, int nphase) {
+  for (int p = 0; p < nphase; ++p) {
+    const double* C = table + (size_t)p * 36;
+    double scale = 0;
+    for (int i = 0; i < 36; ++i) scale = std::max(scale, std::fabs(C[i]));
+    const double tol = 1e-12 * std::max(scale, 1e-300);
+    const double l = C[1], m = C[21];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        double want = 0;
+        if (i < 3 && j < 3) want = (i == j) ? l + 2 * m : l;
+        else if (i == j) want = m;
+        if (std::fabs(C[i * 6 + j] - want) > tol) return false;
+      }
+  }
+  return true;
+}
+}  // namespace
+
+hs_status hs_autotune(const int grid[3], const hs_material* m, const hs_options* base, void* workspace,
+                      size_t workspace_bytes, void* stream, int iters, hs_options* best, double* best_ms) {
+  if (!grid || !m || !m->table || !best || iters < 1) return fail(nullptr, HS_ERR_INVALID_ARG, "bad argument");
+  hs_options b;
+  hs_default_options(&b);
+  if (base) b = *base;
+  const PlanKey key{grid[0], grid[1], grid[2], b.precision, table_isotropic(m->table, m->nphase) ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+      *best = it->second;
+      if (best_ms) *best_ms = -1.0;  // from the cache, not re-timed
+      return HS_OK;
+    }
+  }
+  // candidates: y tile x z chunk (blocks targeted at 512 .. 4096), then the column tile width
+  std::vector<hs_options> cands;
+  const int tys[3] = {2, 4, 8};
+  for (int ty : tys) {
+    if (grid[1] % ty != 0) continue;
+    std::vector<int> zcs;
+    for (int target : {512, 1024, 2048, 4096}) {
+      const int ytiles = grid[1] / ty;
+      const int nz = std::max(1, std::min(grid[2], (target + ytiles - 1) / ytiles));
+      const int zc = (grid[2] + nz - 1) / nz;
+      if (std::find(zcs.begin(), zcs.end(), zc) == zcs.end()) zcs.push_back(zc);
+    }
+    for (int zc : zcs) {
+      hs_options o = b;
+      o.ytile = ty;
+      o.zchunk = zc;
+      cands.push_back(o);
+    }
+  }
+  const double E[6] = {1e-3, 0, 0, 0, 0, 0};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(nullptr, HS_ERR_CUDA, "event create");
+  auto time_one = [&](const hs_options& o, double* ms) -> hs_status {
+    hs_ctx* c = nullptr;
+    hs_status st = hs_create(&c, grid, m, nullptr, &o, workspace, workspace_bytes, stream);
+    if (st != HS_OK) return st;
+    double se[6];
+    int it = 0;
+    double err = 0;
+    st = hs_solve(c, E, 0.0, iters, nullptr, nullptr, se, &it, &err);  // warm-up (and graph capture)
+    if (st >= 0) {
+      cudaEventRecord(e0, s);
+      st = hs_solve(c, E, 0.0, iters, nullptr, nullptr, se, &it, &err);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      *ms = t / std::max(1, it);
+    }
+    hs_destroy(c);
+    return st < 0 ? st : HS_OK;
+  };
+  double best_t = 1e300;
+  hs_options win = b;
+  for (const hs_options& o : cands) {
+    double t = 0;
+    if (time_one(o, &t) == HS_OK && t < best_t) {
+      best_t = t;
+      win = o;
+    }
+  }
+  {
+    hs_options o = win;  // the wider column tile
+    o.col_tile = (b.precision == HS_FP64) ? 8 : 16;
+    double t = 0;
+    if (time_one(o, &t) == HS_OK && t < best_t) {
+      best_t = t;
+      win = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!(best_t < 1e300)) return fail(nullptr, HS_ERR_CUDA, "no candidate ran");
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    g_plans[key] = win;
+  }
+  *best = win;
+  if (best_ms) *best_ms = best_t;
+  return HS_OK;
+}
+
 hs_status hs_get_reference_medium(const hs_ctx* c, double C0[36]) {
   if (!c || !C0) return HS_ERR_INVALID_ARG;
   memcpy(C0, c->C0, sizeof(c->C0));
@@ -1300,6 +1472,8 @@ void hs_destroy(hs_ctx* c) {
     cudaEventDestroy(ev.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& g : c->gexec)
+    if (g) cudaGraphExecDestroy(g);
   delete c;
 }
 

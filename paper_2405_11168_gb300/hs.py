@@ -34,6 +34,7 @@ HS_IDS_U8, HS_IDS_U16 = 0, 1
 # every exported function of include/hs.h
 EXPORTS = [
     "hs_default_options",
+    "hs_autotune",
     "hs_workspace_size",
     "hs_create",
     "hs_solve",
@@ -61,7 +62,7 @@ class hs_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("out_f32", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double), ("zchunk", ctypes.c_int),
                 ("ytile", ctypes.c_int), ("xfuse", ctypes.c_int), ("col_tile", ctypes.c_int),
-                ("col_threads", ctypes.c_int)]
+                ("col_threads", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class HSError(RuntimeError):
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
     lib.hs_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
                               dptr, ctypes.POINTER(hs_options), P, ctypes.c_size_t, P]
     lib.hs_solve.argtypes = [P, dptr, D, I, P, P, dptr, iptr, dptr]
+    lib.hs_autotune.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
+                                ctypes.POINTER(hs_options), P, ctypes.c_size_t, P, I,
+                                ctypes.POINTER(hs_options), dptr]
     lib.hs_solve_stress.argtypes = [P, dptr, D, I, P, P, dptr, dptr, iptr, dptr]
     lib.hs_set_eigenstrain.argtypes = [P, dptr]
     lib.hs_err_history.argtypes = [P, dptr, I, iptr]
@@ -140,6 +144,36 @@ def workspace_size(grid, nphase, opt):
     n = ctypes.c_size_t()
     _check(lib, lib.hs_workspace_size(g, int(nphase), ctypes.byref(opt), ctypes.byref(n)))
     return n.value
+
+
+OPTION_FIELDS = [f for f, _ in hs_options._fields_]
+
+
+def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None, **optkw):
+    """hs_autotune on a device copy of ``ids``; returns (options dict, ms per evaluation or -1 if cached)."""
+    import torch
+
+    lib = load()
+    ids_t = ids if isinstance(ids, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(ids)).to(device)
+    if ids_t.dtype not in (torch.uint8, torch.int16):
+        ids_t = ids_t.to(torch.int16)
+    table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
+    shape = tuple(ids_t.shape)
+    grid = (shape[2], shape[1], shape[0])
+    base = default_options(precision=precision, **optkw)
+    nbytes = workspace_size(grid, table.shape[0], base)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=ids_t.device)
+    ptr = (ws.data_ptr() + 255) & ~255
+    kind = HS_IDS_U8 if ids_t.dtype == torch.uint8 else HS_IDS_U16
+    m = hs_material(kind, ctypes.c_void_p(ids_t.data_ptr()), _dp(table), table.shape[0])
+    st = stream if stream is not None else torch.cuda.current_stream(ids_t.device)
+    best = hs_options()
+    ms = ctypes.c_double()
+    g = (ctypes.c_int * 3)(*grid)
+    _check(lib, lib.hs_autotune(g, ctypes.byref(m), ctypes.byref(base), ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes),
+                                ctypes.c_void_p(st.cuda_stream), int(iters), ctypes.byref(best), ctypes.byref(ms)))
+    torch.cuda.synchronize(ids_t.device)
+    return {f: getattr(best, f) for f in OPTION_FIELDS}, ms.value
 
 
 class Solver:

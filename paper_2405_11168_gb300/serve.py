@@ -1,0 +1,283 @@
+"""Continuous-batching RVE solve service on one GPU.
+
+Requests (a microstructure, its phase table, 1-6 load cases, a precision and a
+tolerance) are queued as they arrive.  Up to ``slots`` requests run at once,
+each on its own CUDA stream and worker thread; a request is admitted, in
+arrival order, when a slot is free and its device memory (solver workspace from
+``hs_workspace_size`` plus field buffers) fits in the HBM budget next to the
+requests already running.  Solves on different streams overlap on the device
+(the C ABI releases the GIL while it waits).  Every kernel reduction is
+deterministic, so a request's results do not depend on what runs beside it.
+
+A request's launch shapes come from the autotuner's plan cache when
+``autotune=True`` (tuned once per grid and precision, then reused).
+
+The batched form of the 6 unit load cases (the columns of the effective
+stiffness, Eqs. final_fields) is a request with ``loads=unit_loads()``.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hs
+
+
+def unit_loads():
+    """The 6 unit macroscopic strains (tensor components); column J of C_eff is <sigma> under load J."""
+    out = []
+    for J in range(6):
+        e = np.zeros(6)
+        e[J] = 1.0 if J < 3 else 0.5
+        out.append(e)
+    return out
+
+
+@dataclass
+class Request:
+    ids: np.ndarray                 # [N3][N2][N1] phase ids (uint8 / uint16)
+    table: np.ndarray               # nphase x 6 x 6 Voigt stiffness
+    loads: list                     # macroscopic strains (6 tensor components each)
+    precision: int = hs.HS_FP32_REFINED
+    tol: float = 1e-6
+    max_iter: int = 5000
+    fields: bool = False            # return eps/sig of the last load case (host arrays)
+    tag: object = None
+    arrival: float = field(default=0.0)
+
+
+@dataclass
+class Result:
+    tag: object
+    sig_eff: np.ndarray             # len(loads) x 6
+    iters: list
+    errs: list
+    status: list
+    eps: np.ndarray = None
+    sig: np.ndarray = None
+    latency_s: float = 0.0
+    queued_s: float = 0.0
+    bytes: int = 0
+
+
+def request_bytes(req: Request) -> int:
+    """Device bytes a request holds while it runs."""
+    n3, n2, n1 = req.ids.shape
+    opt = hs.default_options(precision=req.precision)
+    nb = hs.workspace_size((n1, n2, n3), len(req.table), opt) + 256
+    if req.fields:
+        nb += 2 * 6 * n1 * n2 * n3 * 8
+    nb += n1 * n2 * n3 * 2  # device copy of the ids
+    return nb
+
+
+class Server:
+    def __init__(self, budget_bytes: int, slots: int = 4, device="cuda", autotune: bool = False):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.max_used = 0
+        self.running = 0
+        self.max_running = 0
+        self.autotune = autotune
+        self._cv = threading.Condition()
+        self._pending = collections.deque()
+        self._closed = False
+        self._workers = []
+        for i in range(slots):
+            t = threading.Thread(target=self._worker, name=f"hs-slot-{i}", daemon=True)
+            t.start()
+            self._workers.append(t)
+
+    def submit(self, req: Request) -> Future:
+        need = request_bytes(req)
+        if need > self.budget:
+            raise ValueError(f"request needs {need} bytes, above the budget of {self.budget}")
+        fut = Future()
+        req.arrival = req.arrival or time.perf_counter()
+        with self._cv:
+            if self._closed:
+                raise RuntimeError("server closed")
+            self._pending.append((req, need, fut))
+            self._cv.notify_all()
+        return fut
+
+    def close(self):
+        with self._cv:
+            self._closed = True
+            self._cv.notify_all()
+        for t in self._workers:
+            t.join()
+
+    # admission: the head of the queue runs when its bytes fit next to the running requests
+    def _take(self):
+        with self._cv:
+            while True:
+                if self._pending:
+                    req, need, fut = self._pending[0]
+                    if self.used + need <= self.budget:
+                        self._pending.popleft()
+                        self.used += need
+                        self.running += 1
+                        self.max_used = max(self.max_used, self.used)
+                        self.max_running = max(self.max_running, self.running)
+                        return req, need, fut
+                elif self._closed:
+                    return None
+                self._cv.wait()
+
+    def _release(self, need):
+        with self._cv:
+            self.used -= need
+            self.running -= 1
+            self._cv.notify_all()
+
+    def _worker(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(self.device)
+        while True:
+            item = self._take()
+            if item is None:
+                return
+            req, need, fut = item
+            t_start = time.perf_counter()
+            try:
+                with torch.cuda.stream(stream):
+                    res = self._run(req, stream)
+                stream.synchronize()
+                res.queued_s = t_start - req.arrival
+                res.latency_s = time.perf_counter() - req.arrival
+                res.bytes = need
+                fut.set_result(res)
+            except BaseException as e:  # noqa: BLE001 - report any failure through the future
+                fut.set_exception(e)
+            finally:
+                self._release(need)
+
+    def _run(self, req: Request, stream) -> Result:
+        torch = self.torch
+        ids = torch.from_numpy(np.ascontiguousarray(req.ids)).to(self.device)
+        kw = {}
+        if self.autotune:
+            opts, _ = hs.autotune(ids, req.table, precision=req.precision, device=self.device, stream=stream)
+            kw = {k: opts[k] for k in ("ytile", "zchunk", "col_tile")}
+        s = hs.Solver(ids, req.table, precision=req.precision, device=self.device, stream=stream, **kw)
+        try:
+            sig_eff, iters, errs, status = [], [], [], []
+            out = None
+            for k, E in enumerate(req.loads):
+                last = k == len(req.loads) - 1
+                out = s.solve(E, tol=req.tol, max_iter=req.max_iter, fields=req.fields and last)
+                sig_eff.append(out["sig_eff"])
+                iters.append(out["iters"])
+                errs.append(out["err"])
+                status.append(out["status"])
+            res = Result(tag=req.tag, sig_eff=np.array(sig_eff), iters=iters, errs=errs, status=status)
+            if req.fields:
+                res.eps = out["eps"].cpu().numpy()
+                res.sig = out["sig"].cpu().numpy()
+            return res
+        finally:
+            s.close()
+
+
+def run_stream(server: Server, requests, rate_hz: float, seed: int = 0):
+    """Submit requests with Poisson arrivals at ``rate_hz`` (0: all at once); returns (results, wall s)."""
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    futs = []
+    t_next = t0
+    for req in requests:
+        t_next += rng.exponential(1.0 / rate_hz) if rate_hz > 0 else 0.0
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        req.arrival = time.perf_counter()
+        futs.append(server.submit(req))
+    results = [f.result() for f in futs]
+    return results, time.perf_counter() - t0
+
+
+def latency_stats(results):
+    lat = np.array([r.latency_s for r in results])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean())}
+
+
+def synthetic_requests(n, sizes, seed, precision, tol, max_iter, loads_per_request=(1, 6)):
+    """Seeded request stream: random-sphere two-phase RVEs (contrast log-uniform in
+    1e-3..1e3, plus voids and the rigid surrogate) or 50-grain cubic Voronoi
+    polycrystals, sizes drawn from ``sizes``, 1-6 unit load cases each."""
+    from synth import polycrystal_table, random_rotations, random_spheres, two_phase_table, voronoi_grains
+
+    rng = np.random.default_rng(seed)
+    loads = unit_loads()
+    reqs = []
+    for i in range(n):
+        N = int(rng.choice(sizes))
+        grid = (N, N, N)
+        if rng.random() < 0.5:
+            ids, _ = random_spheres(grid, max(2.0, N / 8.0), 0.2, seed=int(rng.integers(1 << 30)))
+            u = rng.random()
+            contrast = 0.0 if u < 0.05 else (1e6 if u < 0.1 else float(10.0 ** rng.uniform(-3, 3)))
+            table = two_phase_table(1.0, 0.3, contrast, 0.3)
+        else:
+            ids, _ = voronoi_grains(grid, 50, seed=int(rng.integers(1 << 30)))
+            ids = ids.astype(np.uint8)
+            table = polycrystal_table(168.4, 121.4, 75.4, random_rotations(50, seed=int(rng.integers(1 << 30))))
+        k = int(rng.integers(loads_per_request[0], loads_per_request[1] + 1))
+        reqs.append(Request(ids=ids, table=table, loads=loads[:k], precision=precision, tol=tol,
+                            max_iter=max_iter, tag=i))
+    return reqs
+
+
+def main(argv=None):
+    """Serve a seeded synthetic request stream and print one JSON line of throughput and latency."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--sizes", default="32,48,64,96")
+    ap.add_argument("--rate", type=float, default=0.0, help="Poisson arrivals per second (0: all at once)")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--precision", default="refined", choices=["fp64", "fp32", "refined"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=3000)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--seed", type=int, default=5)
+    a = ap.parse_args(argv)
+    prec = {"fp64": hs.HS_FP64, "fp32": hs.HS_FP32, "refined": hs.HS_FP32_REFINED}[a.precision]
+    sizes = [int(x) for x in a.sizes.split(",")]
+    hs.load()
+    reqs = synthetic_requests(a.requests, sizes, a.seed, prec, a.tol, a.max_iter)
+    srv = Server(int(a.budget_gb * 2**30), slots=a.slots, autotune=a.autotune)
+    try:
+        res, wall = run_stream(srv, reqs, a.rate, seed=a.seed)
+    finally:
+        srv.close()
+    solves = sum(len(r.iters) for r in res)
+    conv = sum(int(st == hs.HS_OK) for r in res for st in r.status)
+    line = {"metric": "served RVE solves/s", "value": solves / wall, "unit": "solves/s", "requests": len(res),
+            "solves": solves, "converged": conv, "wall_s": wall, "precision": a.precision, "tol": a.tol,
+            "max_iter": a.max_iter, "sizes": sizes, "rate_hz": a.rate, "slots": a.slots,
+            "budget_gb": a.budget_gb, "max_running": srv.max_running, "max_used_gb": srv.max_used / 2**30,
+            "evaluations": int(sum(sum(r.iters) for r in res)), **latency_stats(res)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+
+    sys.exit(main())
