@@ -558,7 +558,9 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
   const int cur0 = c->cur;
   int cur = cur0;
   const int chunk = std::max(1, c->opt.check_every);
-  const bool graphs = c->opt.use_graphs && !c->prof && !c->xfuse;
+  // the legacy default stream cannot be captured: plain launches there
+  const bool graphs = c->opt.use_graphs && !c->prof && !c->xfuse && c->stream != nullptr &&
+                      c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
   const int gi = (src != nullptr) ? 1 : 0;
   for (;;) {
     if (graphs && c->gexec[gi] != nullptr) {
@@ -568,8 +570,13 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
       if (hst->done) break;
       continue;
     }
-    const bool capture = graphs && c->gchunks[gi] >= 1;
-    if (capture) HS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    bool capture = graphs && c->gchunks[gi] >= 1;
+    if (capture && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      // a stream that refuses capture (e.g. one already being captured): plain launches from now on
+      cudaGetLastError();
+      c->opt.use_graphs = 0;
+      capture = false;
+    }
     for (int i = 0; i < chunk; ++i) {
       if (c->xfuse) {
         hs_status s = launch_force<T>(c, E, cur, src);

@@ -81,7 +81,10 @@ class Server:
         import torch
 
         self.torch = torch
-        self.device = torch.device(device)
+        dev = torch.device(device)
+        if dev.index is None:
+            dev = torch.device(dev.type, torch.cuda.current_device())
+        self.device = dev
         self.budget = int(budget_bytes)
         self.used = 0
         self.max_used = 0
@@ -140,10 +143,22 @@ class Server:
             self.running -= 1
             self._cv.notify_all()
 
+    def _fail_pending(self, exc):
+        with self._cv:
+            while self._pending:
+                _, _, fut = self._pending.popleft()
+                fut.set_exception(exc)
+            self._closed = True
+            self._cv.notify_all()
+
     def _worker(self):
         torch = self.torch
-        torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(self.device)
+        try:
+            torch.cuda.set_device(self.device)
+            stream = torch.cuda.Stream(self.device)
+        except BaseException as e:  # noqa: BLE001 - a slot that cannot start fails the queue, not silently
+            self._fail_pending(e)
+            return
         while True:
             item = self._take()
             if item is None:
@@ -203,7 +218,7 @@ def run_stream(server: Server, requests, rate_hz: float, seed: int = 0):
             time.sleep(delay)
         req.arrival = time.perf_counter()
         futs.append(server.submit(req))
-    results = [f.result() for f in futs]
+    results = [f.result(timeout=3600) for f in futs]
     return results, time.perf_counter() - t0
 
 

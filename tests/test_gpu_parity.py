@@ -257,8 +257,10 @@ def test_graph_replay_matches_plain_launches(hs, prec):
     ids = synth.random_phase_map(grid, 2, seed=3)
     table = synth.two_phase_table(1.0, 0.3, 4.0, 0.3)
     runs = []
+    stream = torch.cuda.Stream()  # a capturable stream (the legacy default stream is not)
+    counted = []
     for graphs in (0, 1):
-        s = hs.Solver(ids, table, precision=prec, check_every=2, use_graphs=graphs)
+        s = hs.Solver(ids, table, precision=prec, check_every=2, use_graphs=graphs, stream=stream)
         res = []
         for E in (E11, E_MIX):
             out = s.solve(E, tol=1e-7, max_iter=200)
@@ -269,7 +271,10 @@ def test_graph_replay_matches_plain_launches(hs, prec):
         res.append((out["iters"], out["err"], out["sig_eff"].copy(), out["eps"].cpu().numpy(),
                     s.err_history().copy()))
         runs.append(res)
+        counted.append(sum(n for _, n in s.profile_read().values()))
         s.close()
+    # replayed chunks are not counted as launches: fewer counted launches with graphs
+    assert counted[1] < counted[0]
     for a, b in zip(*runs):
         assert a[0] == b[0] and a[1] == b[1]
         np.testing.assert_array_equal(a[2], b[2])

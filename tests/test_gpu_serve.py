@@ -40,13 +40,13 @@ def test_same_alone_and_in_the_mix(hs):
     srv = serve.Server(budget_bytes=8 << 30, slots=1)
     try:
         for r in _requests(hs, serve):
-            alone[r.tag] = srv.submit(r).result()
+            alone[r.tag] = srv.submit(r).result(timeout=300)
     finally:
         srv.close()
     srv = serve.Server(budget_bytes=8 << 30, slots=4)
     try:
         futs = [srv.submit(r) for r in _requests(hs, serve)]
-        mix = {f.result().tag: f.result() for f in futs}
+        mix = {f.result(timeout=300).tag: f.result(timeout=300) for f in futs}
     finally:
         srv.close()
     assert srv.max_running >= 2
@@ -66,7 +66,7 @@ def test_admission_respects_the_budget(hs):
     need = max(serve.request_bytes(r) for r in reqs)
     srv = serve.Server(budget_bytes=int(1.5 * need), slots=4)
     try:
-        res = [f.result() for f in [srv.submit(r) for r in reqs]]
+        res = [f.result(timeout=300) for f in [srv.submit(r) for r in reqs]]
     finally:
         srv.close()
     assert srv.max_used <= int(1.5 * need)
