@@ -44,6 +44,11 @@ TOL = 1e-6
 # microstructure, so a step runs every solve to err <= TOL or this budget,
 # whichever comes first, and reports how many reached TOL.
 BUDGET = 64
+# DRAM bytes (read + write) per launch of the dominant kernel at the 256^3
+# workload, from one ncu --set full capture of the current kernel (summarised
+# with its command in profiles/iteration_kernels_256_fp32.md); set to None
+# whenever that kernel changes until it is captured again.
+NCU_TRAFFIC = {"xpass": 632.6e6}
 METRIC = "voxel-iterations/s"
 UNIT = "voxel-iter/s"
 
@@ -331,8 +336,9 @@ def run_ours(args):
                     "frac": ach / 1.25, "traffic": None, "peak_source": "nominal FP64 (GB300)"}
         else:
             ach = b / per_launch_s / 1e9
+            traffic = NCU_TRAFFIC.get(dom_name) if tuple(GRID) == (256, 256, 256) else None
             roof = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
+                    "frac": ach / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs"}
     breakdown = {k: {"ms": round(t, 3), "launches": n,
                      "ms_per_launch": round(t / n, 4) if n else None,
                      "gbs": (round(algorithmic_bytes(k, GRID) / (t / n / 1e3) / 1e9, 1)
