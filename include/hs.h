@@ -41,7 +41,7 @@ typedef enum {
   HS_OK = 0,
   HS_NOT_CONVERGED = 1,        /* max_iter reached; outputs hold the last iterate */
   HS_ERR_INVALID_ARG = -1,     /* bad pointer, size, material, tolerance or load */
-  HS_ERR_UNSUPPORTED_SIZE = -2,/* N_i odd, < 4, > 512, or with a prime factor other than 2, 3 */
+  HS_ERR_UNSUPPORTED_SIZE = -2,/* N_i odd, < 4, > 512, or with a prime factor other than 2, 3, 5, 7, 11 */
   HS_ERR_OOM = -3,             /* the workspace given is smaller than hs_workspace_size() */
   HS_ERR_CUDA = -4,            /* a CUDA call failed (see hs_last_error) */
   HS_DIVERGED = -5,            /* err became NaN/Inf or grew 1e6x above its minimum */
@@ -73,7 +73,8 @@ typedef struct {
   int ytile;            /* y rows per block of the x-pass: 0 = automatic, or 2, 4, 8 dividing N2 */
   int xfuse;            /* 0: x-direction FFTs in their own row passes around a real-space stencil
                            pass (default); 1: one fused x-pass (inverse x FFT, stencil, forward x FFT) */
-  int col_tile;         /* y/z FFT tile width in complex columns: 0 = automatic; FP32 8 or 16, FP64 4 or 8 */
+  int col_tile;         /* y/z FFT tile width in complex columns: 0 = automatic; FP32 8 or 16, FP64 4 or 8
+                           (grids with a factor 5, 7 or 11: the automatic width, and xfuse = 0) */
   int col_threads;      /* threads per y/z FFT block: 0 = automatic; a multiple of 32, at most 768 (FP32)
                            or 384 (FP64) */
   int use_graphs;       /* 1 (default): after its first chunk, a solve replays its iteration chunks

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhs.so")
-UNITS = ["capi.cu", "kernels_util.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu"]
+UNITS = ["capi.cu", "kernels_util.cu", "kernels_f32.cu", "kernels_f64.cu", "kernels_ext_f32.cu",
+         "kernels_ext_f64.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -52,6 +52,9 @@ bool make_plan(int L, FftPlan* p) {
     if (!push(2)) return false;
   while (r % 3 == 0)
     if (!push(3)) return false;
+  for (int R : {5, 7, 11})
+    while (r % R == 0)
+      if (!push(R)) return false;
   return r == 1 && p->nstage > 0;
 }
 
@@ -1004,6 +1007,15 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
   c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
   c->smem_z = (size_t)c->n3 * 3 * c->ct * cs;
   c->xfuse = (o.xfuse == 1);
+  {
+    // radix-5/7/11 lengths run the split path with the default column tile only
+    const bool ext = hs::plan_ext(c->plan[0]) || hs::plan_ext(c->plan[1]) || hs::plan_ext(c->plan[2]);
+    if (ext && (c->xfuse || c->ct != (c->f64 ? 4 : 8))) {
+      delete c;
+      return fail(nullptr, HS_ERR_UNSUPPORTED_SIZE,
+                  "grids with a factor 5, 7 or 11 need xfuse = 0 and the default column tile");
+    }
+  }
   c->nthr_row = 256;
   for (int m = 0; m < 2; ++m) c->smem_row[m] = hs::row_layout(m, c->n1, c->P, c->nthr_row, c->f64 ? 8 : 4).total;
   const int xtiles = (c->nh + c->ct - 1) / c->ct;

@@ -139,7 +139,8 @@ __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T
 }
 
 // LF > 0: the transformed length is LF and the block has NT threads, both
-// fixed at compile time (hot sizes); LF = 0: both taken at run time.
+// fixed at compile time (hot sizes); LF = 0: both taken at run time; LF = -1:
+// run time, plans with a radix-5, 7 or 11 stage.
 template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArgs<T> a) {
   using C = typename cplx_t<T>::type;
@@ -205,15 +206,16 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
     }
     return;
   }
+  constexpr bool EXT = LF < 0;
   if (MODE == COL_Y_INV || MODE == COL_Z_INV_STATE) {
-    HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
+    fft_smem<true, true, EXT>(sm, 1, W, -1, W, plan.L, plan.nstage, plan.packed, tw, tid, nthr);
   } else {
-    HS_FFT_COLS(false, sm, W, W, plan, tw, tid, nthr);
+    fft_smem<false, true, EXT>(sm, 1, W, -1, W, plan.L, plan.nstage, plan.packed, tw, tid, nthr);
   }
   if (MODE == COL_Z_GREEN) {
     col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
     __syncthreads();
-    HS_FFT_COLS(true, sm, W, W, plan, tw, tid, nthr);
+    fft_smem<true, true, EXT>(sm, 1, W, -1, W, plan.L, plan.nstage, plan.packed, tw, tid, nthr);
   }
   for (int i = tid; i < L * W; i += nthr) {
     const int e = i / W, rem = i - e * W, c = rem / CT, col = rem - c * CT;

@@ -1,4 +1,4 @@
-// Batched mixed-radix (2/3/4/8/16) complex FFTs on sequences held in shared memory.
+// Batched mixed-radix (2/3/4/8/16, and 5/7/11) complex FFTs on sequences held in shared memory.
 //
 // Self-sorting Stockham formulation, one radix-R butterfly per (thread, step):
 // stage s with radix R and Ns = R_1...R_{s-1} reads x[b + m L/R], multiplies by
@@ -10,7 +10,9 @@
 // Threads per sequence: ceil(L/kE) with kE = 8 elements per thread, so a
 // thread never holds more than ceil(kE/R) butterflies of one stage; radices
 // are 8, 4, 3 and 2 (a radix-16 DFT is available but keeps too many values
-// live for the generic stage loop).  Sequence s, element e lives at
+// live for the generic stage loop), and 5, 7 and 11 for the other supported
+// lengths: their length-R DFT is the plain O(R^2) sum with coefficients
+// w_R^{mk} = w_L^{(L/R)(mk mod R)} read from the same twiddle table.  Sequence s, element e lives at
 // buf[s*ss + e*es].  Forward = exp(-2 pi i nk/L), inverse = exp(+...), both
 // unnormalised.  Twiddles come from a per-axis table w_L^j = exp(-2 pi i j/L),
 // j < L, computed on the host.
@@ -208,12 +210,29 @@ __device__ __forceinline__ void stockham_stage(C* buf, int ss, int es, int ps, i
           v[k][m] = cmul(v[k][m], w);
         }
       }
-      Dft<R, INV, C>::run(v[k]);
       const int base = pq * Ns * R + kk;
+      if constexpr (R == 5 || R == 7 || R == 11) {
+        // table DFT: each output straight to its place (no array of R outputs kept live)
+        const int tstep = L / R;
+#pragma unroll 1
+        for (int q = 0; q < R; ++q) {
+          C acc = v[k][0];
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int e = base + m * Ns;
-        sb[e * es + (ps >= 0 ? (e >> ps) : 0)] = v[k][m];
+          for (int m = 1; m < R; ++m) {
+            C w = __ldg(tw + tstep * ((m * q) % R));
+            if (INV) w.y = -w.y;
+            acc = cadd(acc, cmul(v[k][m], w));
+          }
+          const int e = base + q * Ns;
+          sb[e * es + (ps >= 0 ? (e >> ps) : 0)] = acc;
+        }
+      } else {
+        Dft<R, INV, C>::run(v[k]);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int e = base + m * Ns;
+          sb[e * es + (ps >= 0 ? (e >> ps) : 0)] = v[k][m];
+        }
       }
     }
   }
@@ -228,7 +247,9 @@ __device__ __forceinline__ void stockham_stage(C* buf, int ss, int es, int ps, i
 // on sequence g0 + i % G (lanes walk across sequences: for column tiles whose
 // sequences are adjacent in memory, ss = 1).  Either way a warp's shared-memory
 // accesses stay (nearly) free of bank conflicts.
-template <bool INV, bool COLMAP, typename C>
+// EXT: also radices 5, 7, 11 (their stages keep more values live, so only the
+// kernels instantiated for such lengths carry them).
+template <bool INV, bool COLMAP, bool EXT = false, typename C>
 __device__ __forceinline__ void fft_smem(C* buf, int ss, int es, int ps, int nseq, int L, int nstage, int packed,
                                          const C* __restrict__ tw, int tid, int nthreads) {
   const int T = (L + kE - 1) / kE;
@@ -248,6 +269,9 @@ __device__ __forceinline__ void fft_smem(C* buf, int ss, int es, int ps, int nse
       if (R == 8) stockham_stage<8, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
       else if (R == 4) stockham_stage<4, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
       else if (R == 3) stockham_stage<3, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
+      else if (EXT && R == 5) stockham_stage<EXT ? 5 : 2, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
+      else if (EXT && R == 7) stockham_stage<EXT ? 7 : 2, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
+      else if (EXT && R == 11) stockham_stage<EXT ? 11 : 2, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
       else stockham_stage<2, INV>(buf, ss, es, ps, s, t, T, active, L, Ns, nsh, tw, wsync);
       Ns *= R;
       nsh = (nsh >= 0 && (R & (R - 1)) == 0) ? nsh + (R == 8 ? 3 : R == 4 ? 2 : 1) : -1;
@@ -261,6 +285,15 @@ __host__ __device__ __forceinline__ int rpitch(int n) { return n + (n >> 3) + 1;
 
 #define HS_FFT_ROWS(INV, buf, pitch, nseq, plan, tw, tid, nthr)                                       \
   ::hs::fft_smem<INV, false>(buf, pitch, 1, 3, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
+// a plan with a radix-5, 7 or 11 stage
+__host__ __device__ inline bool plan_ext(const FftPlan& p) {
+  for (int st = 0; st < p.nstage; ++st) {
+    const int R = (p.packed >> (4 * st)) & 15;
+    if (R == 5 || R == 7 || R == 11) return true;
+  }
+  return false;
+}
+
 #define HS_FFT_COLS(INV, buf, W, nseq, plan, tw, tid, nthr) \
   ::hs::fft_smem<INV, true>(buf, 1, W, -1, nseq, (plan).L, (plan).nstage, (plan).packed, tw, tid, nthr)
 

@@ -1,0 +1,3 @@
+// FP32 row and column passes for grids with a radix-5, 7 or 11 factor.
+#include "kernels_impl.cuh"
+HS_INSTANTIATE_EXT(float, 8)

@@ -1,6 +1,7 @@
 // Definitions of the launchers in launch.h; included once per precision.
 #pragma once
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "launch.h"
@@ -98,7 +99,9 @@ static cudaError_t stencil_ty(const MarchArgs<float>& a, bool iso, int mode, dim
   return stencil_one<TY, MatAnisoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
 }
 
-// FP32 real-space pass (FORCE / FIELDS on a real displacement field)
+// FP32 real-space pass (FORCE / FIELDS on a real displacement field); a
+// template so that only the unit that launches it instantiates its kernels
+template <int UNUSED = 0>
 static cudaError_t stencil_f32(const MarchArgs<float>& a, bool iso, int ty, int mode, dim3 g, int nthr,
                                size_t smem, cudaStream_t s) {
   if (mode != MODE_FORCE && mode != MODE_FIELDS) return cudaErrorInvalidValue;
@@ -120,13 +123,11 @@ static cudaError_t col_one(const ColArgs<T>& a, dim3 g, int nthr, size_t smem, c
 }
 
 // real-displacement passes: the packed FP32 kernel, or k_march for FP64
-static inline cudaError_t march_real_dispatch(const MarchArgs<float>& a, bool iso, int ty, int mode, dim3 g,
-                                              int nthr, size_t smem, cudaStream_t s) {
-  return stencil_f32(a, iso, ty, mode, g, nthr, smem, s);
-}
-static inline cudaError_t march_real_dispatch(const MarchArgs<double>& a, bool iso, int ty, int mode, dim3 g,
-                                              int nthr, size_t smem, cudaStream_t s) {
-  return march_real<double, true>(a, iso, ty, mode, g, nthr, smem, s);
+template <typename T>
+static cudaError_t march_real_dispatch(const MarchArgs<T>& a, bool iso, int ty, int mode, dim3 g, int nthr,
+                                      size_t smem, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) return stencil_f32<>(a, iso, ty, mode, g, nthr, smem, s);
+  else return march_real<double, true>(a, iso, ty, mode, g, nthr, smem, s);
 }
 
 template <typename T, int CT, int LF = 0, int NT = 0>
@@ -242,6 +243,7 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
                             cudaStream_t s) {                                                            \
     if (a.buf == nullptr || a.tw == nullptr || ((mode == COL_Z_GREEN || mode == COL_Z_INV_STATE) && a.S == nullptr)) \
       return cudaErrorInvalidValue;                                                                      \
+    if (plan_ext(a.plan)) return launch_col_ext<T>(a, mode, ct, grid, nthr, smem, s);                  \
     if (ct == (CT)) return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                  \
     if (ct == (CT) / 2) return col_dispatch<T, (CT) / 2, NT>(a, mode, grid, nthr, smem, s);              \
     return cudaErrorInvalidValue;                                                                        \
@@ -251,11 +253,13 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     if (a.tw == nullptr || (mode == ROW_C2R ? (a.spec_in == nullptr || (a.real_out == nullptr && a.acc64 == nullptr)) \
                                             : (a.real_in == nullptr || a.spec_out == nullptr)))         \
       return cudaErrorInvalidValue;                                                                      \
+    if (plan_ext(a.plan)) return launch_row_ext<T>(a, mode, nb, nthr, smem, s);                        \
     return mode == ROW_C2R ? row_dispatch<T, ROW_C2R>(a, nb, nthr, smem, s)                             \
                            : row_dispatch<T, ROW_R2C>(a, nb, nthr, smem, s);                            \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t row_blocks_per_sm<T>(int mode, int n1, int nthr, size_t smem, int* n) {                     \
+    if (n1 % 5 == 0 || n1 % 7 == 0 || n1 % 11 == 0) return row_blocks_per_sm_ext<T>(mode, nthr, smem, n);  \
     return mode == ROW_C2R ? row_occ<T, ROW_C2R>(n1, nthr, smem, n) : row_occ<T, ROW_R2C>(n1, nthr, smem, n); \
   }                                                                                                      \
   template <>                                                                                            \
@@ -271,5 +275,26 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     size_t nrows = (size_t)3 * n3 * n2, n = nrows * P;                                                   \
     k_state_import<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, S, nrows, nh, P);                  \
     return cudaGetLastError();                                                                           \
+  }                                                                                                      \
+  }
+
+// Kernels for plans with a radix-5, 7 or 11 stage, in their own translation unit.
+#define HS_INSTANTIATE_EXT(T, CT)                                                                         \
+  namespace hs {                                                                                         \
+  template <>                                                                                            \
+  cudaError_t launch_col_ext<T>(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, \
+                                cudaStream_t s) {                                                        \
+    if (ct != (CT)) return cudaErrorInvalidValue;                                                        \
+    return col_ct<T, CT, -1>(a, mode, grid, nthr, smem, s);                                              \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_row_ext<T>(const RowArgs<T>& a, int mode, int nb, int nthr, size_t smem, cudaStream_t s) { \
+    return mode == ROW_C2R ? row_one<T, ROW_C2R, -1>(a, nb, nthr, smem, s)                               \
+                           : row_one<T, ROW_R2C, -1>(a, nb, nthr, smem, s);                              \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t row_blocks_per_sm_ext<T>(int mode, int nthr, size_t smem, int* n) {                        \
+    return mode == ROW_C2R ? row_occ_one<T, ROW_C2R, -1>(nthr, smem, n)                                  \
+                           : row_occ_one<T, ROW_R2C, -1>(nthr, smem, n);                                 \
   }                                                                                                      \
   }

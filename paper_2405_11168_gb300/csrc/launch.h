@@ -23,6 +23,14 @@ cudaError_t launch_col(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nth
 template <typename T>
 cudaError_t launch_row(const RowArgs<T>& a, int mode, int nblocks, int nthr, size_t smem, cudaStream_t s);
 
+// the same passes for plans with a radix-5, 7 or 11 stage (default column tile only)
+template <typename T>
+cudaError_t launch_col_ext(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_row_ext(const RowArgs<T>& a, int mode, int nblocks, int nthr, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t row_blocks_per_sm_ext(int mode, int nthr, size_t smem, int* n);
+
 // resident blocks per SM of the row pass (persistent grid sizing)
 template <typename T>
 cudaError_t row_blocks_per_sm(int mode, int n1, int nthr, size_t smem, int* n);

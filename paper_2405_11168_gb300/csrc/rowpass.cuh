@@ -89,7 +89,8 @@ __device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& 
 // Persistent: block j transforms batches j, j + gridDim.x, ...; the copy of the
 // next batch runs while the current one is transformed.
 // LF > 0: N1 = LF and 256 threads per block, fixed at compile time (hot
-// sizes); LF = 0: both taken at run time.
+// sizes); LF = 0: both taken at run time; LF = -1: run time, plans with a
+// radix-5, 7 or 11 stage.
 template <typename T, int MODE, int LF = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowArgs<T> a) {
   using C = typename cplx_t<T>::type;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       if constexpr (LF > 0) {
         fft_fixed<LF, true, false, LF, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
       } else {
-        fft_smem<true, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
+        fft_smem<true, false, (LF < 0)>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                               tid, nthr);
       }
       if (bulk) {
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       if constexpr (LF > 0) {
         fft_fixed<LF, false, false, LF, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
       } else {
-        fft_smem<false, false>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
+        fft_smem<false, false, (LF < 0)>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                                tid, nthr);
       }
       if (bulk) {

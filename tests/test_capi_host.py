@@ -47,8 +47,9 @@ def test_default_options_and_status_strings(lib):
 
 
 @pytest.mark.parametrize("grid,ok", [((32, 32, 32), True), ((48, 24, 12), True), ((6, 4, 8), True),
-                                     ((31, 32, 32), False), ((2, 4, 4), False), ((40, 32, 32), False),
-                                     ((1024, 32, 32), False), ((44, 44, 44), False)])
+                                     ((31, 32, 32), False), ((2, 4, 4), False), ((40, 32, 32), True),
+                                     ((1024, 32, 32), False), ((44, 44, 44), True), ((26, 32, 32), False),
+                                     ((40, 28, 22), True)])
 def test_workspace_size_validates_grid(lib, grid, ok):
     from paper_2405_11168_gb300 import hs
 

@@ -280,3 +280,28 @@ def test_graph_replay_matches_plain_launches(hs, prec):
         np.testing.assert_array_equal(a[2], b[2])
         np.testing.assert_array_equal(a[3], b[3])
         np.testing.assert_array_equal(a[4], b[4])
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 2e-5)])
+@pytest.mark.parametrize("grid,kind", [((44, 44, 44), "sphere"), ((40, 28, 22), "random"), ((10, 14, 22), "random")])
+def test_radix_5_7_11_grids(hs, prec, tol, grid, kind):
+    """Axis lengths with factors 5, 7 and 11, among them the 44^3 sphere (R = 17.6, nu = 0.125)
+    of the contrast study in Section 3.4: the same iterates as the oracle."""
+    if kind == "sphere":
+        ids = synth.centred_sphere(grid, radius=17.6)
+        table = synth.two_phase_table(1.0, 0.125, 20.0, 0.125)
+        C0 = None
+        lam0 = T.c0_alpha_rule(table)
+    else:
+        ids = synth.random_phase_map(grid, 2, seed=sum(grid))
+        table = synth.two_phase_table(1.0, 0.3, 6.0, 0.3)
+        C0 = synth.isotropic_voigt(3.5, 0.3)
+        lam0 = T.stiffness_tensor(C0)
+    s = hs.Solver(ids, table, C0=C0, precision=prec)
+    out = s.solve(E_MIX, tol=0.0, max_iter=5)
+    ref = T.solve_alg1(ids, table, lam0, T.strain_tensor_from_voigt(E_MIX), tol=0.0, max_iter=5)
+    np.testing.assert_allclose(s.err_history(), ref.errs, rtol=1e-9 if prec == 0 else tol)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < tol
+    assert rel(out["sig"].cpu().numpy(), s_ref) < tol
+    s.close()
