@@ -67,7 +67,9 @@ typedef struct {
   int out_f32;          /* field outputs as float (1) or double (0) */
   int inner_max;        /* HS_FP32_REFINED: max FP32 iterations per correction solve */
   double inner_ratio;   /* HS_FP32_REFINED: a correction solve stops when its force norm is
-                           below inner_ratio times the FP64 residual's */
+                           below inner_ratio times the FP64 residual's; the first solve (from
+                           u = 0, the plain FP32 basic scheme) when its error falls to
+                           inner_ratio times its first error */
   int zchunk;           /* z planes per block of the x-pass (0 = automatic; a tiling knob that
                            does not change results beyond rounding order) */
   int ytile;            /* y rows per block of the x-pass: 0 = automatic, or 2, 4, 8 dividing N2 */
@@ -158,8 +160,9 @@ hs_status hs_solve_stress(hs_ctx* c, const double S[6], double tol, int max_iter
  * Errors: HS_ERR_INVALID_ARG (non-finite values), HS_ERR_CUDA. */
 hs_status hs_set_eigenstrain(hs_ctx* c, const double* eps0);
 
-/* Error after each residual evaluation of the last hs_solve (HS_FP32_REFINED: of each FP64
- * residual sweep).  Writes min(n, available) values; *n_written gets the count. */
+/* Error after each residual evaluation of the last hs_solve (HS_FP32_REFINED: the FP32
+ * evaluations of its first, plain solve, then one value per FP64 residual sweep).
+ * Writes min(n, available) values; *n_written gets the count. */
 hs_status hs_err_history(const hs_ctx* c, double* out, int n, int* n_written);
 
 /* Displacement state u(q) after the last solve, as complex128 [3][N3][N2][N1/2+1]

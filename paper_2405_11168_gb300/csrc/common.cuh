@@ -33,6 +33,9 @@ struct DevStatus {
   // S0 (sigma^a - <sigma>).
   const double* macro;
   double E[6];
+  // > 0: also converged once err <= rel_tol * (err of the first evaluation of this run)
+  double rel_tol;
+  double err_first;
 };
 
 enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
@@ -144,7 +147,8 @@ __device__ inline void reduce_and_finalize(const double (&acc)[NRED], double* pa
       st->done = DONE_DIVERGED;
     } else {
       if (k == 0 || err < st->err_min) st->err_min = err;
-      if (err < st->tol) st->done = DONE_CONVERGED;
+      if (k == 0) st->err_first = err;
+      if (err < st->tol || (st->rel_tol > 0 && err <= st->rel_tol * st->err_first)) st->done = DONE_CONVERGED;
       else if (err > 1e6 * st->err_min && k > 10) st->done = DONE_DIVERGED;
       else if (k + 1 >= st->max_iter) st->done = DONE_MAXITER;
     }
