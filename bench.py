@@ -48,7 +48,7 @@ BUDGET = 64
 # workload, from one ncu --set full capture of the current kernel (summarised
 # with its command in profiles/iteration_kernels_256_fp32.md); set to None
 # whenever that kernel changes until it is captured again.
-NCU_TRAFFIC = {"xpass": 632.6e6}
+NCU_TRAFFIC = {"xpass": None}
 METRIC = "voxel-iterations/s"
 UNIT = "voxel-iter/s"
 
@@ -152,8 +152,10 @@ def algorithmic_bytes(kind, grid, refined=True):
     N = n1 * n2 * n3
     nh = n1 // 2 + 1
     comp = n3 * n2 * nh * 8           # one FP32 complex half-spectrum component
-    if kind == "xpass":               # real-space stencil: u in, ids, correction source, force out
-        return 3 * N * 4 + 2 * N + (3 * N * 4 if refined else 0) + 3 * N * 4
+    if kind == "xpass":               # real-space stencil: u in, ids, force out
+        return 3 * N * 4 + 2 * N + 3 * N * 4
+    if kind == "xpass_src":           # the same in a correction solve, which also reads the FP32 source
+        return 3 * N * 4 + 2 * N + 3 * N * 4 + 3 * N * 4
     if kind == "x_inv":
         return 3 * comp + 3 * N * 4
     if kind == "x_fwd":

@@ -190,7 +190,9 @@ enum {
   HS_K_OTHER = 6,     /* state transforms, correction accumulation, set-up */
   HS_K_XINV = 7,      /* inverse x FFT (half spectrum -> real rows), xfuse = 0 */
   HS_K_XFWD = 8,      /* forward x FFT (real rows -> half spectrum), xfuse = 0 */
-  HS_K_COUNT = 9
+  HS_K_XPASS_SRC = 9, /* real-space pass of a correction solve (reads the FP32 correction source;
+                         HS_FP32_REFINED) */
+  HS_K_COUNT = 10
 };
 
 /* Start (on != 0) or stop per-launch timing: every kernel launch of this context is then
@@ -201,7 +203,7 @@ hs_status hs_profile_enable(hs_ctx* c, int on);
 /* Accumulated device time (ms, from the events) and launch counts per kernel class since the
  * last read or enable; resets the accumulators.  ms and launches have HS_K_COUNT entries.
  * Launch counts are kept whether or not timing is enabled. */
-hs_status hs_profile_read(hs_ctx* c, double ms[9], long long launches[9]);
+hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
 
 /* Limits of hs_residual_noalloc's fixed scratch array. */
 #define HS_NOALLOC_SCRATCH_BYTES (512 * 1024) /* bytes held on every device that loads the library */

@@ -461,7 +461,7 @@ template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], con
   const size_t sm = march_smem(c->n1, c->ty, sizeof(T) == 8, mode, true, src != nullptr);
   cudaError_t e;
   {
-    LaunchScope ls(c, mode == hs::MODE_FORCE ? HS_K_XPASS : HS_K_FIELDS);
+    LaunchScope ls(c, mode == hs::MODE_FORCE ? (src != nullptr ? HS_K_XPASS_SRC : HS_K_XPASS) : HS_K_FIELDS);
     e = hs::launch_march<T>(a, c->iso, c->ty, mode, true, c->grid_m, c->nthr_m, sm, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(real)");
@@ -1502,7 +1502,7 @@ hs_status hs_profile_enable(hs_ctx* c, int on) {
   return HS_OK;
 }
 
-hs_status hs_profile_read(hs_ctx* c, double ms[7], long long launches[7]) {
+hs_status hs_profile_read(hs_ctx* c, double ms[HS_K_COUNT], long long launches[HS_K_COUNT]) {
   if (!c || !ms || !launches) return HS_ERR_INVALID_ARG;
   for (int k = 0; k < HS_K_COUNT; ++k) ms[k] = 0;
   cudaError_t e = cudaStreamSynchronize(c->stream);

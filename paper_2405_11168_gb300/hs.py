@@ -28,7 +28,7 @@ HS_DIVERGED = -5
 HS_ERR_TIMEOUT = -6
 
 HS_FP64, HS_FP32, HS_FP32_REFINED = 0, 1, 2
-KERNEL_CLASSES = ["xpass", "y_fwd", "z_green", "y_inv", "resid64", "fields", "other", "x_inv", "x_fwd"]
+KERNEL_CLASSES = ["xpass", "y_fwd", "z_green", "y_inv", "resid64", "fields", "other", "x_inv", "x_fwd", "xpass_src"]
 HS_IDS_U8, HS_IDS_U16 = 0, 1
 
 # every exported function of include/hs.h
