@@ -684,7 +684,7 @@ hs_status launch_residual64(hs_ctx* c, const double E[6], int mode, void* eps, v
   a.out_f32 = c->opt.out_f32;
   a.skip_if_done = 0;
   const size_t sm = march_smem(c->n1, c->ty64, true, mode, true);
-  LaunchScope ls(c, mode == hs::MODE_FORCE ? HS_K_RESID64 : HS_K_FIELDS);
+  LaunchScope ls(c, mode == hs::MODE_FIELDS ? HS_K_FIELDS : HS_K_RESID64);
   cudaError_t e = hs::launch_march<double>(a, c->iso, c->ty64, mode, true, c->grid_m64, c->nthr_m, sm, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(residual fp64)");
   return HS_OK;
@@ -761,10 +761,15 @@ hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter,
     s = c->xfuse ? launch_emit(c, 0) : launch_rows<float>(c, hs::ROW_C2R, c->u64, false);
     if (s != HS_OK) return s;
   }
+  bool fields_done = false;
   for (;;) {
     hs_status s = reset_status(c, 0.0, 1 << 30, 0.0, E);
     if (s != HS_OK) return s;
-    s = launch_residual64(c, E, hs::MODE_FORCE, nullptr, nullptr);
+    // a sweep that uses up the evaluation budget is the last: it also writes the fields
+    const bool last = (total + 1 >= max_iter) && eps != nullptr && sig != nullptr;
+    s = last ? launch_residual64(c, E, hs::MODE_FORCE_FIELDS, eps, sig)
+             : launch_residual64(c, E, hs::MODE_FORCE, nullptr, nullptr);
+    fields_done = last;
     if (s != HS_OK) return s;
     s = read_status(c, &h64);
     if (s != HS_OK) return s;
@@ -805,7 +810,7 @@ hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter,
     s = c->xfuse ? launch_emit(c, 0) : launch_rows<float>(c, hs::ROW_C2R, c->u64, false);
     if (s != HS_OK) return s;
   }
-  if (eps != nullptr && sig != nullptr) {
+  if (eps != nullptr && sig != nullptr && !fields_done) {
     hs_status s = launch_residual64(c, E, hs::MODE_FIELDS, eps, sig);
     if (s != HS_OK) return s;
   }

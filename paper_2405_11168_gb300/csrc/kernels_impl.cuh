@@ -47,6 +47,14 @@ static cudaError_t march_ty(const MarchArgs<T>& a, bool iso, int mode, dim3 g, i
     if (REAL) return cudaErrorInvalidValue;
     return march_one<T, TY, MatIso<T>, MODE_EMIT, false>(a, MatIso<T>{a.mat}, g, nthr, smem, s);
   }
+  if (mode == MODE_FORCE_FIELDS) {  // last FP64 residual sweep of a refined solve
+    if constexpr (REAL && sizeof(T) == 8) {
+      if (iso) return march_one<T, TY, MatIso<T>, MODE_FORCE_FIELDS, REAL>(a, MatIso<T>{a.mat}, g, nthr, smem, s);
+      return march_one<T, TY, MatAniso<T>, MODE_FORCE_FIELDS, REAL>(a, MatAniso<T>{a.mat}, g, nthr, smem, s);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (iso) {
     MatIso<T> m{a.mat};
     if (mode == MODE_FORCE) return march_one<T, TY, MatIso<T>, MODE_FORCE, REAL>(a, m, g, nthr, smem, s);
@@ -234,7 +242,8 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     if (!real && a.in == nullptr) return cudaErrorInvalidValue;                                          \
     if (mode == MODE_EMIT && a.u64 == nullptr) return cudaErrorInvalidValue;                             \
     if (mode == MODE_FORCE && !real && a.out == nullptr) return cudaErrorInvalidValue;                   \
-    if (mode == MODE_FIELDS && (a.eps_out == nullptr || a.sig_out == nullptr)) return cudaErrorInvalidValue; \
+    if ((mode == MODE_FIELDS || mode == MODE_FORCE_FIELDS) && (a.eps_out == nullptr || a.sig_out == nullptr)) \
+      return cudaErrorInvalidValue;                                                                      \
     if (real) return march_real_dispatch(a, iso, ty, mode, grid, nthr, smem, s);                         \
     return march_real<T, false>(a, iso, ty, mode, grid, nthr, smem, s);                                  \
   }                                                                                                      \

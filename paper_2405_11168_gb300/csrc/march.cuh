@@ -28,7 +28,9 @@
 
 namespace hs {
 
-enum { MODE_FORCE = 0, MODE_FIELDS = 1, MODE_EMIT = 2 };
+// MODE_FORCE_FIELDS: MODE_FORCE that also writes the fields of MODE_FIELDS (the
+// last FP64 residual sweep of a refined solve)
+enum { MODE_FORCE = 0, MODE_FIELDS = 1, MODE_EMIT = 2, MODE_FORCE_FIELDS = 3 };
 
 template <typename T> struct MarchArgs {
   using C = typename cplx_t<T>::type;
@@ -426,7 +428,8 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
     HS_FFT_ROWS(true, ring, rpitch(n1), NSI, plan, tw1, tid, nthr);
     __syncthreads();
   }
-  const int pend = (MODE == MODE_FORCE) ? z0 + zc : z0 + zc - 1;
+  constexpr bool FORCE_LIKE = (MODE == MODE_FORCE || MODE == MODE_FORCE_FIELDS);
+  const int pend = FORCE_LIKE ? z0 + zc : z0 + zc - 1;
   for (int p = z0; p <= pend; ++p) {
     const int ib = (p - z0) & 1;  // ids buffer of voxel plane p, source buffer of output plane p-1
     int sc, sp;
@@ -435,12 +438,12 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
     if (REAL) {
       sc = (p - z0 + 1) % 3;
       sp = (p - z0) % 3;
-      if (p < pend) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, (p - z0 + 2) % 3, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
+      if (p < pend) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, (p - z0 + 2) % 3, ib ^ 1, FORCE_LIKE ? p : -1, true);
     } else {
       sc = (p - z0 + 1) & 1;
       sp = sc ^ 1;
       march_pack<T, TY>(mp, ring, x, xact, sc);
-      if (p < pend) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, 0, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
+      if (p < pend) march_prefetch<T, TY, REAL>(mp, tid, nthr, p + 1, 0, ib ^ 1, FORCE_LIKE ? p : -1, true);
       HS_FFT_ROWS(true, ring + sc * NSI * rpitch(n1), rpitch(n1), NSI, plan, tw1, tid, nthr);
       __syncthreads();
     }
@@ -527,6 +530,29 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
         if (acc_sig) {
 #pragma unroll
           for (int i = 0; i < 6; ++i) sacc[i] += sv[i];
+        }
+        if constexpr (MODE == MODE_FORCE_FIELDS) {
+          // eps = 1/2 (eps^T1 + eps^T2) (tensor components), sigma = 1/2 (sigma^T1 + sigma^T2):
+          // T1's halves are stored, T2's added to them
+          if (acc_sig) {
+            const size_t o = (size_t)pz * rplane + (size_t)((y0 + jj - 1) % n2) * n1 + x;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              const T eh = T(0.5) * ev[i] * (i < 3 ? T(1) : T(0.5));
+              const T sh = T(0.5) * sv[i];
+              if (a.out_f32) {
+                float* ep = reinterpret_cast<float*>(a.eps_out) + i * rcomp + o;
+                float* sp = reinterpret_cast<float*>(a.sig_out) + i * rcomp + o;
+                if (tt == 0) { *ep = (float)eh; *sp = (float)sh; }
+                else { *ep = (float)((T)*ep + eh); *sp = (float)((T)*sp + sh); }
+              } else {
+                double* ep = reinterpret_cast<double*>(a.eps_out) + i * rcomp + o;
+                double* sp = reinterpret_cast<double*>(a.sig_out) + i * rcomp + o;
+                if (tt == 0) { *ep = (double)eh; *sp = (double)sh; }
+                else { *ep += (double)eh; *sp += (double)sh; }
+              }
+            }
+          }
         }
         T l0[3], l1[3];
         // per force component k: (sigma_1k, sigma_2k, sigma_3k)
@@ -659,7 +685,7 @@ __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT m
       for (int k = 0; k < 3; ++k) { Fp[r][k] = Fn[r][k]; Fn[r][k] = 0; }
   }
   cp_async_wait_all();
-  if (MODE != MODE_FORCE) return;
+  if (!FORCE_LIKE) return;
   double acc[NRED];
 #pragma unroll
   for (int i = 0; i < 6; ++i) acc[i] = (double)sacc[i];
