@@ -23,7 +23,7 @@ only non-elementary step; the fields stored in q-space are kept on the half
 spectrum ``h1 = 0..N1/2`` because every transformed field is the transform of a
 real field on the integer strain grid.
 
-Readings of the paper taken here (each is also listed in the design doc):
+Readings of the paper taken here (where it is ambiguous or garbled):
 
 1. Eq. (Dq) drops closing parentheses; each term is read as
    ``exp(i/2 (+-q1 +-q2 +-q3))``, signs as printed.
