@@ -161,6 +161,8 @@ static cudaError_t col_dispatch(const ColArgs<T>& a, int mode, dim3 g, int nthr,
   if (nthr == NT) {
     if (L == 256) return col_ct<T, CT, 256, NT>(a, mode, g, nthr, smem, s);
     if (L == 512) return col_ct<T, CT, 512, NT>(a, mode, g, nthr, smem, s);
+    if (L == 128) return col_ct<T, CT, 128, NT>(a, mode, g, nthr, smem, s);
+    if (L == 64) return col_ct<T, CT, 64, NT>(a, mode, g, nthr, smem, s);
   }
   return col_ct<T, CT>(a, mode, g, nthr, smem, s);
 }
@@ -187,6 +189,8 @@ static cudaError_t row_occ(int n1, int nthr, size_t smem, int* n) {
   if (nthr == 256) {
     if (n1 == 256) return row_occ_one<T, MODE, 256>(nthr, smem, n);
     if (n1 == 512) return row_occ_one<T, MODE, 512>(nthr, smem, n);
+    if (n1 == 128) return row_occ_one<T, MODE, 128>(nthr, smem, n);
+    if (n1 == 64) return row_occ_one<T, MODE, 64>(nthr, smem, n);
   }
   return row_occ_one<T, MODE>(nthr, smem, n);
 }
@@ -197,6 +201,8 @@ static cudaError_t row_dispatch(const RowArgs<T>& a, int nb, int nthr, size_t sm
   if (nthr == 256) {
     if (a.n1 == 256) return row_one<T, MODE, 256>(a, nb, nthr, smem, s);
     if (a.n1 == 512) return row_one<T, MODE, 512>(a, nb, nthr, smem, s);
+    if (a.n1 == 128) return row_one<T, MODE, 128>(a, nb, nthr, smem, s);
+    if (a.n1 == 64) return row_one<T, MODE, 64>(a, nb, nthr, smem, s);
   }
   return row_one<T, MODE>(a, nb, nthr, smem, s);
 }

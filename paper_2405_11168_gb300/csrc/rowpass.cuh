@@ -103,8 +103,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
   const int G = L.G;                           // sequences per batch
   const int grp = tid / T8, t = tid - grp * T8;
   const bool wsync = T8 <= 32 && (32 % T8) == 0;
-  // fixed lengths: unpadded rows with the XOR swizzle; otherwise one spare slot per 8
-  const int pitch = LF > 0 ? LF : rpitch(n1);
+  // fixed lengths: XOR-swizzled rows (length-64 rows 72 apart, so that the
+  // four rows a warp transforms fall on different banks); otherwise one spare
+  // slot per 8
+  constexpr int FP = LF == 64 ? 72 : (LF > 0 ? LF : 1);
+  const int pitch = LF > 0 ? FP : rpitch(n1);
   C* z = reinterpret_cast<C*>(smraw) + (size_t)grp * pitch;
   auto zi = [](int e) { return LF > 0 ? rswz(e) : rpad(e); };
   const int nseq = a.nrows / 2;
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       }
       group_sync(wsync);
       if constexpr (LF > 0) {
-        fft_fixed<LF, true, false, LF, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+        fft_fixed<LF, true, false, FP, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
       } else {
         fft_smem<true, false, (LF < 0)>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                               tid, nthr);
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       }
       group_sync(wsync);
       if constexpr (LF > 0) {
-        fft_fixed<LF, false, false, LF, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+        fft_fixed<LF, false, false, FP, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
       } else {
         fft_smem<false, false, (LF < 0)>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                                tid, nthr);

@@ -104,9 +104,10 @@ def test_z_chunking_and_column_groups(hs, prec, zchunk):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("grid", [(256, 512, 4), (512, 6, 256), (4, 256, 512)])
+@pytest.mark.parametrize("grid", [(256, 512, 4), (512, 6, 256), (4, 256, 512), (128, 64, 6), (64, 6, 128),
+                                  (6, 128, 64)])
 def test_hot_length_compiled_variants(hs, prec, grid):
-    """Axis lengths 256 and 512 run FFT kernels whose plan, strides and block
+    """Axis lengths 64, 128, 256 and 512 run FFT kernels whose plan, strides and block
     size are fixed at compile time (rows along x, columns along y and z); each
     such kernel here meets a generic one on another axis.  Same iterates as
     the oracle."""
