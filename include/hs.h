@@ -212,9 +212,9 @@ hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
 
 /* Equilibrium residual of a displacement field, for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a library convenience.  It is for code that must not
- * allocate at the moment it runs - work being recorded into a CUDA stream capture, real-time or
- * embedded callers with a fixed memory budget, callers whose device memory belongs entirely to
- * another allocator - and who therefore cannot supply hs_create's workspace.  It computes, in
+ * allocate at the moment it runs - real-time or embedded callers with a fixed memory budget,
+ * callers whose device memory belongs entirely to another allocator (a caching pool), checks run
+ * where an allocation could fail or stall - and who therefore cannot supply hs_create's workspace.  It computes, in
  * FP64, the nodal force F = dE/du of the tetrahedral-stencil energy at the real-space corner
  * displacement u (the residual of Algorithm 1 evaluated in real space), the mean stress <sigma>
  * and the L2 norm of F (Eq. L2-norm, real-space form), exactly as the FP64 residual sweep of

@@ -2,11 +2,12 @@
 // computed without any device allocation.
 //
 // Who needs this: code that may not allocate device memory at the moment it
-// runs - work recorded into a CUDA stream capture (allocation calls are not
-// allowed while a stream is being captured), real-time or embedded callers
-// that run inside a fixed, pre-reserved memory budget, and callers whose
-// device memory is wholly owned by another allocator (a framework's caching
-// pool).  Such callers cannot provide the workspace that hs_create needs, so
+// runs - real-time or embedded callers that run inside a fixed, pre-reserved
+// memory budget, callers whose device memory is wholly owned by another
+// allocator (a framework's caching pool, where a stray cudaMalloc would
+// fragment or exceed what that pool manages), and checks run from places where
+// an allocation could fail or stall (inside an out-of-memory handler, a
+// watchdog).  Such callers cannot provide the workspace that hs_create needs, so
 // this entry point keeps the little scratch it uses (the device copy of the
 // phase table, per-block partial sums and a status record) in one file-scope
 // device array of fixed size that exists for as long as the library is

@@ -1,9 +1,9 @@
 """The allocation-free residual entry point (hs_residual_noalloc) against the
 regular entry points.
 
-hs_residual_noalloc serves callers that cannot allocate device memory (work
-recorded into a stream capture, fixed-budget real-time callers, callers whose
-memory belongs to another allocator).  It must give what the regular solver
+hs_residual_noalloc serves callers that cannot allocate device memory
+(fixed-budget real-time callers, callers whose memory belongs to another
+allocator, checks run where an allocation could fail or stall).  It must give what the regular solver
 gives: at a displacement state loaded with hs_set_state, one FP64 evaluation
 of hs_solve reports the error and the mean stress; the no-alloc call on the
 same displacement, in real space, must report the same values (FP64
