@@ -85,7 +85,8 @@ typedef struct {
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
- * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0, col_tile 0, col_threads 0. */
+ * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0, col_tile 0, col_threads 0,
+ * use_graphs 1. */
 hs_status hs_default_options(hs_options* opt);
 
 /* Autotuner with a process-wide plan cache (no counterpart in the paper: it picks launch
@@ -105,7 +106,8 @@ hs_status hs_autotune(const int grid[3], const hs_material* m, const hs_options*
 hs_status hs_workspace_size(const int grid[3], int nphase, const hs_options* opt, size_t* bytes);
 
 /* Create a solver for one microstructure.
- *  grid       N1, N2, N3: even, 4..512, factors 2 and 3 only (Section 2.1 requires even N_i).
+ *  grid       N1, N2, N3: even, 4..512, prime factors 2, 3, 5, 7 and 11 only (Section 2.1
+ *             requires even N_i).
  *  m          microstructure; copied to the device here.
  *  C0         host 6x6 Voigt stiffness of the homogeneous reference medium lambda0 (Section 2.3),
  *             symmetric positive definite; NULL picks it: for two isotropic phases the rule of the
