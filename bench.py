@@ -193,6 +193,141 @@ def cpu_sample(ids, table, workers=None):
     return one
 
 
+class TorchFFTPipeline:
+    """Library comparison: the same basic-scheme iteration (Algorithm 1) written
+    with torch.fft (cuFFT on a GPU) and torch elementwise operations, in the
+    real-space stencil form the CUDA path uses.  Not part of the library: the
+    bench times it beside the CUDA kernels.
+
+    State: the corner-indexed displacement spectrum u(q), complex
+    [3][N3][N2][N1/2+1].  One iteration: u(r) by an unnormalised inverse FFT;
+    for each tetrahedron the unscaled differences 2 D_i u_j over its four
+    corners (Eqs. DA1-DA2), the engineering strain E + deps^T, the stress
+    lambda(r) : strain (Algorithm 1 step 3); the nodal force
+    F_k = 1/4 sum_T sum_corners sum_i c_i sigma^T_ik (the adjoint of the
+    stencil, Eq. der_E_dep_Q); L2 = sqrt(sum |F|^2 / N), err = L2 / ||<sigma>||
+    (Eqs. L2-norm, tolerance); F(q) by a 1/N forward FFT and
+    u(q) <- u(q) - 2 Omega(q) F(q) (Algorithm 1 step 5, 2 F(q) = f(q)), with
+    Omega^-1 = (lambda0 + mu0) M + mu0 tr(M) I, M_jk = 2 Re(D_j conj D_k)
+    for the isotropic reference medium, and Omega = 0 at q = 0 and q = (pi, pi, pi).
+
+    Two isotropic phases (a 6x6 table per phase with C = 0 for a void);
+    reference medium by the Section 3.4 rule (same nu as the matrix,
+    k0 = a k_m + (1 - a) k_i, a = 0.55 if k_i < k_m else 0.45).
+    """
+
+    # corners of each tetrahedron as (shift (ox, oy, oz): corner index = voxel
+    # index - shift, coefficients c_i of 2 D_i u = sum_corners c_i u(corner))
+    TETRA = (
+        (((0, 0, 0), (1, 1, 1)), ((0, 1, 1), (1, -1, -1)), ((1, 1, 0), (-1, -1, 1)), ((1, 0, 1), (-1, 1, -1))),
+        (((0, 1, 0), (1, -1, 1)), ((0, 0, 1), (1, 1, -1)), ((1, 1, 1), (-1, -1, -1)), ((1, 0, 0), (-1, 1, 1))),
+    )
+    # Voigt index of the tensor component (i, k)
+    VOIGT = ((0, 5, 4), (5, 1, 3), (4, 3, 2))
+
+    def __init__(self, ids, table, device, dtype=None):
+        import torch
+
+        self.torch = torch
+        self.dtype = dtype or torch.float32
+        self.cdtype = torch.complex64 if self.dtype == torch.float32 else torch.complex128
+        table = np.asarray(table, dtype=np.float64)
+        n3, n2, n1 = ids.shape
+        self.grid = (n1, n2, n3)
+        self.N = n1 * n2 * n3
+        lam = table[:, 0, 1]
+        mu = table[:, 3, 3]
+        idt = torch.as_tensor(np.ascontiguousarray(ids).astype(np.int64), device=device)
+        self.lam = torch.as_tensor(lam, dtype=self.dtype, device=device)[idt]
+        self.mu = torch.as_tensor(mu, dtype=self.dtype, device=device)[idt]
+        # reference medium (Section 3.4 rule)
+        k_m, k_i = lam[0] + 2 * mu[0] / 3, lam[1] + 2 * mu[1] / 3
+        a = 0.55 if k_i < k_m else 0.45
+        k0 = a * k_m + (1 - a) * k_i
+        nu0 = lam[0] / (2 * (lam[0] + mu[0]))
+        mu0 = 3 * k0 * (1 - 2 * nu0) / (2 * (1 + nu0))
+        lam0 = k0 - 2 * mu0 / 3
+        # Omega(q) in FP64, stored in the working precision: [3][3][N3][N2][N1/2+1]
+        h1 = np.arange(n1 // 2 + 1)[None, None, :]
+        h2 = np.arange(n2)[None, :, None]
+        h3 = np.arange(n3)[:, None, None]
+        q = (2 * np.pi * h1 / n1, 2 * np.pi * h2 / n2, 2 * np.pi * h3 / n3)
+        D = np.zeros((3, n3, n2, n1 // 2 + 1), dtype=np.complex128)
+        for shift, c in self.TETRA[0]:
+            ph = np.exp(-1j * (shift[0] * q[0] + shift[1] * q[1] + shift[2] * q[2]))
+            for i in range(3):
+                D[i] = D[i] + 0.5 * c[i] * ph
+        M = 2.0 * np.real(D[:, None] * np.conj(D[None, :]))
+        Oi = (lam0 + mu0) * M + mu0 * np.trace(M)[None, None] * np.eye(3)[:, :, None, None, None]
+        Oi = np.moveaxis(Oi, (0, 1), (-2, -1))
+        sing = np.zeros(Oi.shape[:3], dtype=bool)
+        sing[0, 0, 0] = True
+        if n1 % 2 == 0 and n2 % 2 == 0 and n3 % 2 == 0:
+            sing[n3 // 2, n2 // 2, n1 // 2] = True
+        Oi[sing] = np.eye(3)
+        Om = np.linalg.inv(Oi)
+        Om[sing] = 0.0
+        self.Om = torch.as_tensor(np.moveaxis(Om, (-2, -1), (0, 1)).copy(), dtype=self.dtype, device=device)
+        self.uh = torch.zeros((3, n3, n2, n1 // 2 + 1), dtype=self.cdtype, device=device)
+        self.C = [torch.tensor([c for _, c in tet], dtype=self.dtype, device=device) for tet in self.TETRA]
+
+    def step(self, E):
+        """One evaluation + update; returns (err, <sigma> Voigt)."""
+        torch = self.torch
+        n1, n2, n3 = self.grid
+        Eeng = [float(E[i]) * (1.0 if i < 3 else 2.0) for i in range(6)]
+        u = torch.fft.irfftn(self.uh, s=(n3, n2, n1), dim=(1, 2, 3), norm="forward")
+        F = torch.zeros_like(u)
+        ssum = torch.zeros(6, dtype=torch.float64, device=u.device)
+        for tet, C in zip(self.TETRA, self.C):
+            U = torch.stack([torch.roll(u, shifts=(sh[2], sh[1], sh[0]), dims=(1, 2, 3)) for sh, _ in tet])
+            g = torch.einsum("vi,vj...->ij...", C, U)  # g[i][j] = 2 D_i u_j
+            e = [Eeng[0] + 0.5 * g[0, 0], Eeng[1] + 0.5 * g[1, 1], Eeng[2] + 0.5 * g[2, 2],
+                 Eeng[3] + 0.5 * (g[1, 2] + g[2, 1]), Eeng[4] + 0.5 * (g[0, 2] + g[2, 0]),
+                 Eeng[5] + 0.5 * (g[0, 1] + g[1, 0])]
+            del U, g
+            lt = self.lam * (e[0] + e[1] + e[2])
+            m2 = 2 * self.mu
+            s = [lt + m2 * e[0], lt + m2 * e[1], lt + m2 * e[2], self.mu * e[3], self.mu * e[4], self.mu * e[5]]
+            ssum += torch.stack([torch.sum(x, dtype=torch.float64) for x in s])
+            S = torch.stack([s[self.VOIGT[i][k]] for i in range(3) for k in range(3)]).view((3, 3) + u.shape[1:])
+            contrib = torch.einsum("vi,ik...->vk...", C, S)  # sum_i c_i sigma_ik per corner
+            for v, (sh, _) in enumerate(tet):
+                F += torch.roll(contrib[v], shifts=(-sh[2], -sh[1], -sh[0]), dims=(1, 2, 3))
+        F *= 0.25
+        l2 = torch.sqrt(torch.sum(F * F, dtype=torch.float64) / self.N)
+        sm = 0.5 * ssum / self.N
+        nrm = torch.sqrt(torch.sum(sm[:3] ** 2) + 2 * torch.sum(sm[3:] ** 2))
+        Fh = torch.fft.rfftn(F, dim=(1, 2, 3), norm="forward")
+        for j in range(3):
+            self.uh[j] -= 2 * (self.Om[j, 0] * Fh[0] + self.Om[j, 1] * Fh[1] + self.Om[j, 2] * Fh[2])
+        return l2 / nrm, sm
+
+
+def time_torch_pipeline(ids, table, device, iters, warmup=2):
+    """ms per iteration of TorchFFTPipeline on the device (CUDA events)."""
+    import torch
+
+    p = TorchFFTPipeline(ids, table, device)
+    E = unit_loads()[0]
+    for _ in range(warmup):
+        p.step(E)
+    stream = torch.cuda.current_stream(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    ev0.record(stream)
+    for _ in range(iters):
+        err, _ = p.step(E)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1) / iters
+    last = float(err)
+    del p
+    torch.cuda.empty_cache()
+    return ms, last
+
+
 def combine_over_ranks(ms, iters, device, world):
     """Replicas: the job's time is the slowest rank's, its work the sum of all ranks'."""
     if world <= 1:
@@ -367,6 +502,23 @@ def run_ours(args):
                "h2d_bytes_per_step": int(len(tables) * (ids.nbytes + 2 * 36 * 8)),
                "d2h_bytes_per_step": int(len(tables) * 6 * 6 * 8)}
 
+    # the same iteration through torch.fft (cuFFT) and torch elementwise kernels, outside the timed region
+    lib_base = None
+    if rank == 0 and not args.skip_torch:
+        for s in solvers:
+            s.close()
+        solvers = []
+        torch.cuda.empty_cache()
+        t_ms, t_err = time_torch_pipeline(ids, tables[0], dev, iters=TORCH_ITERS)
+        ours_ms = sum(t / n for k, (t, n) in prof.items() if n and k in ("xpass", "y_fwd", "z_green", "y_inv",
+                                                                       "x_inv", "x_fwd"))
+        lib_base = {"value": N / (t_ms / 1e3), "unit": UNIT, "ms_per_iter": round(t_ms, 3),
+                    "kind": "torch.fft (cuFFT) + torch elementwise ops, FP32, the same iteration",
+                    "sample": f"{TORCH_ITERS} iterations of the {GRID[0]}^3 contrast-{CONTRASTS[0]:g} E11 solve "
+                              f"(err after them {t_err:.3e})",
+                    "ours_fp32_ms_per_iter": round(ours_ms, 4),
+                    "speedup_fp32_iteration": round(t_ms / ours_ms, 2) if ours_ms else None}
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cores = os.cpu_count() or 1
@@ -387,6 +539,10 @@ def run_ours(args):
             "solves_converged": f"{sum(c for c, _ in timed_conv)}/{len(timed_conv)}",
             "final_err_max": max(e for _, e in timed_conv),
             "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+            "model_frac": {"bytes_per_voxel_iter": MODEL_BYTES, "frac": value * MODEL_BYTES / (peak * 1e9),
+                           "what": "voxel-iter/s x the 4-pass model's bytes per FP32 voxel-iteration "
+                                   "(30 x 4 B + 1 B) / measured HBM peak"},
+            "torch_fft_baseline": lib_base,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -396,6 +552,12 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     return 0
 
+
+# Bytes per FP32 voxel-iteration of the minimal 4-pass pipeline model (three
+# complex half-spectrum components read and written by four passes, the state
+# read and written once, a one-byte phase id): 30 x 4 + 1.
+MODEL_BYTES = 121
+TORCH_ITERS = 10
 
 # FP64 operations per voxel of the real-space residual sweep (isotropic phases):
 # 2 tetrahedra x (gradient 3x6 adds + 3 x 3 scalings + 9 adds/doublings for the
@@ -412,6 +574,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-torch", action="store_true", help="skip the torch.fft comparison pipeline")
     ap.add_argument("--grid", type=int, default=256, help="cubic grid size (profiling runs use smaller cases)")
     ap.add_argument("--ncontrast", type=int, default=4, help="use the first k contrasts (profiling runs)")
     args = ap.parse_args()
