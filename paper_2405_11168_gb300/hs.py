@@ -122,6 +122,26 @@ def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _ids_tensor(ids, device):
+    """Phase ids as a contiguous device tensor the C ABI can read: uint8 stays
+    uint8 (HS_IDS_U8); every other integer type becomes 16-bit (HS_IDS_U16,
+    int16 carrying the uint16 bit pattern)."""
+    import torch
+
+    t = ids if isinstance(ids, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(ids))
+    if t.dtype.is_floating_point or t.dtype.is_complex or t.dtype == torch.bool:
+        raise TypeError(f"phase ids must be an integer array, got {t.dtype}")
+    if t.dim() != 3:
+        raise ValueError(f"phase ids must be [N3][N2][N1], got shape {tuple(t.shape)}")
+    if t.dtype != torch.uint8 and t.dtype != torch.int16:
+        if t.numel() and (int(t.min()) < 0 or int(t.max()) > 65535):
+            raise ValueError("phase ids must lie in 0..65535")
+        t = t.to(torch.int32).to(torch.int16)  # wraps 32768..65535 to the same 16-bit pattern
+    t = t.to(device).contiguous()
+    kind = HS_IDS_U8 if t.dtype == torch.uint8 else HS_IDS_U16
+    return t, kind
+
+
 def _check(lib, s, ctx=None):
     if s < 0:
         msg = lib.hs_last_error(ctx).decode() if ctx is not None else lib.hs_last_error(None).decode()
@@ -154,9 +174,8 @@ def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None,
     import torch
 
     lib = load()
-    ids_t = ids if isinstance(ids, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(ids)).to(device)
-    if ids_t.dtype not in (torch.uint8, torch.int16):
-        ids_t = ids_t.to(torch.int16)
+    dev = ids.device if isinstance(ids, torch.Tensor) and ids.is_cuda else torch.device(device)
+    ids_t, kind = _ids_tensor(ids, dev)
     table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
     shape = tuple(ids_t.shape)
     grid = (shape[2], shape[1], shape[0])
@@ -164,9 +183,9 @@ def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None,
     nbytes = workspace_size(grid, table.shape[0], base)
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=ids_t.device)
     ptr = (ws.data_ptr() + 255) & ~255
-    kind = HS_IDS_U8 if ids_t.dtype == torch.uint8 else HS_IDS_U16
     m = hs_material(kind, ctypes.c_void_p(ids_t.data_ptr()), _dp(table), table.shape[0])
     st = stream if stream is not None else torch.cuda.current_stream(ids_t.device)
+    st.wait_stream(torch.cuda.current_stream(ids_t.device))
     best = hs_options()
     ms = ctypes.c_double()
     g = (ctypes.c_int * 3)(*grid)
@@ -197,13 +216,23 @@ class Solver:
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) & ~255
         if ids_t is None:
+            # host ids: hs_create copies them to the device
             ids_np = np.ascontiguousarray(ids)
+            if ids_np.ndim != 3 or ids_np.dtype.kind not in "iu":
+                raise TypeError(f"phase ids must be an integer [N3][N2][N1] array, got {ids_np.dtype} "
+                                f"{ids_np.shape}")
             kind = HS_IDS_U8 if ids_np.dtype == np.uint8 else HS_IDS_U16
+            if kind == HS_IDS_U16 and ids_np.size and (ids_np.min() < 0 or ids_np.max() > 65535):
+                raise ValueError("phase ids must lie in 0..65535")
             ids_np = ids_np.astype(np.uint8 if kind == HS_IDS_U8 else np.uint16, copy=False)
             ids_ptr = ids_np.ctypes.data
             self._ids_keep = ids_np
         else:
-            kind = HS_IDS_U8 if ids_t.dtype == torch.uint8 else HS_IDS_U16
+            dev = ids_t.device if ids_t.is_cuda else torch.device(device)
+            ids_t, kind = _ids_tensor(ids_t, dev)
+            # hs_create reads the ids on the solver's stream: order it after the work
+            # that produced them (and any conversion above) on the current stream
+            self.stream.wait_stream(torch.cuda.current_stream(ids_t.device))
             ids_ptr = ids_t.data_ptr()
             self._ids_keep = ids_t
         self._table = table
@@ -284,7 +313,11 @@ class Solver:
         return out
 
     def set_state(self, uhat):
-        uhat = uhat.contiguous()
+        n1, n2, n3 = self.grid
+        if tuple(uhat.shape) != (3, n3, n2, n1 // 2 + 1):
+            raise ValueError(f"state must be [3][N3][N2][N1/2+1], got {tuple(uhat.shape)}")
+        uhat = uhat.to(device=self.workspace.device, dtype=self.torch.complex128).contiguous()
+        self.stream.wait_stream(self.torch.cuda.current_stream(uhat.device))
         self._state_keep = uhat
         _check(self.lib, self.lib.hs_set_state(self.ctx, ctypes.c_void_p(uhat.data_ptr())), self.ctx)
 

@@ -94,3 +94,29 @@ def test_create_rejects_bad_arguments_before_any_device_work(lib):
                       ctypes.byref(opt), fake_ws, 1 << 30, None)
     assert s == hs.HS_ERR_INVALID_ARG
     assert ctx.value is None
+
+
+def test_binding_normalises_phase_ids_for_the_c_abi():
+    """The binding hands the C ABI only uint8 or 16-bit contiguous ids, and
+    refuses ids it would otherwise misread (floats, negatives, > 65535)."""
+    torch = pytest.importorskip("torch")
+    from paper_2405_11168_gb300 import hs
+
+    cpu = torch.device("cpu")
+    for dt, kind in ((torch.uint8, hs.HS_IDS_U8), (torch.int16, hs.HS_IDS_U16), (torch.int32, hs.HS_IDS_U16),
+                     (torch.int64, hs.HS_IDS_U16)):
+        t = torch.arange(60, dtype=torch.int64).reshape(3, 4, 5).to(dt).transpose(1, 2)
+        out, k = hs._ids_tensor(t, cpu)
+        assert k == kind and out.is_contiguous()
+        assert torch.equal(out.to(torch.int64), t.to(torch.int64))
+    out, k = hs._ids_tensor(torch.tensor([0, 40000, 65535]).reshape(1, 1, 3), cpu)
+    assert k == hs.HS_IDS_U16
+    assert (out.to(torch.int32) & 0xFFFF).tolist() == [[[0, 40000, 65535]]]
+    with pytest.raises(ValueError):
+        hs._ids_tensor(torch.tensor([-1, 0]).reshape(1, 1, 2), cpu)
+    with pytest.raises(ValueError):
+        hs._ids_tensor(torch.tensor([65536]).reshape(1, 1, 1), cpu)
+    with pytest.raises(TypeError):
+        hs._ids_tensor(torch.zeros(2, 2, 2), cpu)
+    with pytest.raises(ValueError):
+        hs._ids_tensor(torch.zeros(4, 4, dtype=torch.uint8), cpu)
