@@ -216,11 +216,11 @@ hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
  * The paper has no counterpart: this is a library convenience.  It is for code that must not
  * allocate at the moment it runs - real-time or embedded callers with a fixed memory budget,
  * callers whose device memory belongs entirely to another allocator (a caching pool), checks run
- * where an allocation could fail or stall - and who therefore cannot supply hs_create's workspace.  It computes, in
- * FP64, the nodal force F = dE/du of the tetrahedral-stencil energy at the real-space corner
- * displacement u (the residual of Algorithm 1 evaluated in real space), the mean stress <sigma>
- * and the L2 norm of F (Eq. L2-norm, real-space form), exactly as the FP64 residual sweep of
- * HS_FP32_REFINED does.
+ * where an allocation could fail or stall - and who therefore cannot supply hs_create's
+ * workspace.  It computes, in FP64, the nodal force F = dE/du of the tetrahedral-stencil energy
+ * at the real-space corner displacement u (the residual of Algorithm 1 evaluated in real space),
+ * the mean stress <sigma> and the L2 norm of F (Eq. L2-norm, real-space form), exactly as the
+ * FP64 residual sweep of HS_FP32_REFINED does.
  *  grid       N1, N2, N3 as for hs_create.
  *  ids        device, uint16 phase ids [N3][N2][N1].
  *  table      host, nphase x 36 Voigt stiffness (as hs_material.table); 1 <= nphase <= HS_NOALLOC_MAX_PHASES.
