@@ -81,7 +81,8 @@ typedef struct {
                            or 384 (FP64) */
   int use_graphs;       /* 1 (default): after its first chunk, a solve replays its iteration chunks
                            (check_every iterations) as one captured CUDA graph; 0: plain launches.
-                           Profiling (hs_profile_enable) always uses plain launches. */
+                           With profiling on (hs_profile_enable) the captured chunk also records the
+                           per-kernel events, read back after each replay. */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,

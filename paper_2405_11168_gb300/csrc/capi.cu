@@ -223,6 +223,11 @@ struct hs_ctx {
   // captured iteration chunks: [0] full problem, [1] correction solves (refined)
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   int gchunks[2] = {0, 0};   // uncaptured chunks run so far (capture follows the first)
+  bool gexec_prof[2] = {false, false};       // the captured chunk records profiling events
+  long long glaunches[2][HS_K_COUNT] = {};  // kernel launches per replay, by class
+  bool capturing = false;                    // inside the stream capture of chunk cap_gi
+  int cap_gi = 0;
+  bool gprof_ok = true;                      // event timing of replayed chunks works here
   bool dev_macro = false;    // plain modes under applied stress: E lives in the device status
   double Einit[6] = {0, 0, 0, 0, 0, 0};
   FftPlan plan[3];
@@ -247,6 +252,8 @@ struct hs_ctx {
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> ev_used;
   std::vector<cudaEvent_t> ev_pool;
+  std::vector<Ev> gev[2];            // events recorded by the nodes of captured chunk [gi]
+  double prof_ms[HS_K_COUNT] = {};   // kernel time of replayed chunks, read after each replay
 };
 
 namespace {
@@ -261,18 +268,25 @@ hs_status cuda_fail(hs_ctx* c, cudaError_t e, const char* where) {
   return fail(c, HS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Bracket one kernel launch: count it and, when profiling, record events.
+// Bracket one kernel launch: count it and, when profiling, record events.  Inside
+// the stream capture of an iteration chunk the launch is counted per replay and
+// the events become event-record nodes of the graph, read after each replay.
 struct LaunchScope {
   hs_ctx* c;
   int kind;
   cudaEvent_t a = nullptr, b = nullptr;
   LaunchScope(hs_ctx* c_, int kind_) : c(c_), kind(kind_) {
-    c->launches[kind]++;
+    if (c->capturing) c->glaunches[c->cap_gi][kind]++;
+    else c->launches[kind]++;
     if (c->prof) {
       a = take();
       b = take();
-      if (a) cudaEventRecord(a, c->stream);
+      if (a) record(a);
     }
+  }
+  void record(cudaEvent_t e) {
+    if (c->capturing) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->stream);
   }
   cudaEvent_t take() {
     cudaEvent_t e = nullptr;
@@ -286,14 +300,44 @@ struct LaunchScope {
   }
   ~LaunchScope() {
     if (a && b) {
-      cudaEventRecord(b, c->stream);
-      c->ev_used.push_back({kind, a, b});
+      record(b);
+      (c->capturing ? c->gev[c->cap_gi] : c->ev_used).push_back({kind, a, b});
     } else {
       if (a) c->ev_pool.push_back(a);
       if (b) c->ev_pool.push_back(b);
     }
   }
 };
+
+// Forget captured chunk gi: its graph, its profiling events and its launch counts.
+void drop_graph(hs_ctx* c, int gi, bool reset_chunks) {
+  if (c->gexec[gi]) cudaGraphExecDestroy(c->gexec[gi]);
+  c->gexec[gi] = nullptr;
+  c->gexec_prof[gi] = false;
+  for (auto& ev : c->gev[gi]) {
+    c->ev_pool.push_back(ev.a);
+    c->ev_pool.push_back(ev.b);
+  }
+  c->gev[gi].clear();
+  for (int k = 0; k < HS_K_COUNT; ++k) c->glaunches[gi][k] = 0;
+  if (reset_chunks) c->gchunks[gi] = 0;
+}
+
+// After a replay of chunk gi has completed (the stream was synchronised): count its
+// launches and add the times its event nodes recorded.
+void account_replay(hs_ctx* c, int gi) {
+  for (int k = 0; k < HS_K_COUNT; ++k) c->launches[k] += c->glaunches[gi][k];
+  if (!c->gexec_prof[gi]) return;
+  for (auto& ev : c->gev[gi]) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess) {
+      c->prof_ms[ev.kind] += t;
+    } else {
+      cudaGetLastError();
+      c->gprof_ok = false;  // profile with plain launches from now on
+    }
+  }
+}
 
 #define HS_CU(c, call)                                    \
   do {                                                    \
@@ -564,23 +608,45 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
   int cur = cur0;
   const int chunk = std::max(1, c->opt.check_every);
   // the legacy default stream cannot be captured: plain launches there
-  const bool graphs = c->opt.use_graphs && !c->prof && !c->xfuse && c->stream != nullptr &&
+  const bool graphs = c->opt.use_graphs && !(c->prof && !c->gprof_ok) && !c->xfuse && c->stream != nullptr &&
                       c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
   const int gi = (src != nullptr) ? 1 : 0;
+  // a chunk captured with profiling on or off is recaptured when that changes
+  if (c->gexec[gi] != nullptr && c->gexec_prof[gi] != c->prof) drop_graph(c, gi, false);
   for (;;) {
     if (graphs && c->gexec[gi] != nullptr) {
       HS_CU(c, cudaGraphLaunch(c->gexec[gi], c->stream));
       hs_status s = read_status(c, hst);
       if (s != HS_OK) return s;
+      account_replay(c, gi);
       if (hst->done) break;
       continue;
     }
     bool capture = graphs && c->gchunks[gi] >= 1;
-    if (capture && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      // a stream that refuses capture (e.g. one already being captured): plain launches from now on
-      cudaGetLastError();
-      c->opt.use_graphs = 0;
-      capture = false;
+    if (capture) {
+      drop_graph(c, gi, false);
+      if (c->prof) {
+        // the capture's event nodes take their events from the pool: two per launch, at most
+        // six launches per iteration; created here, outside the capture
+        while (c->ev_pool.size() < (size_t)12 * chunk) {
+          cudaEvent_t ev = nullptr;
+          if (cudaEventCreate(&ev) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+          }
+          c->ev_pool.push_back(ev);
+        }
+      }
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        // a stream that refuses capture (e.g. one already being captured): plain launches from now on
+        cudaGetLastError();
+        c->opt.use_graphs = 0;
+        capture = false;
+      }
+    }
+    if (capture) {
+      c->capturing = true;
+      c->cap_gi = gi;
     }
     for (int i = 0; i < chunk; ++i) {
       if (c->xfuse) {
@@ -596,10 +662,12 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
         if (s == HS_OK) s = launch_cols<T>(c, 0);
         if (s != HS_OK) {
           if (capture) {
+            c->capturing = false;
             cudaGraph_t g = nullptr;
             cudaStreamEndCapture(c->stream, &g);
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
+            drop_graph(c, gi, false);
           }
           return s;
         }
@@ -607,18 +675,24 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
     }
     if (capture) {
       // the captured chunk has not run yet: instantiate it, keep it, and launch it
+      c->capturing = false;
       cudaGraph_t g = nullptr;
-      HS_CU(c, cudaStreamEndCapture(c->stream, &g));
+      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
       cudaGraphExec_t ex = nullptr;
-      cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        drop_graph(c, gi, false);
+        return cuda_fail(c, e, "graph capture");
+      }
       c->gexec[gi] = ex;
+      c->gexec_prof[gi] = c->prof;
       HS_CU(c, cudaGraphLaunch(ex, c->stream));
     }
     ++c->gchunks[gi];
     hs_status s = read_status(c, hst);
     if (s != HS_OK) return s;
+    if (capture) account_replay(c, gi);
     if (hst->done) break;
   }
   *last_in = c->xfuse ? (cur0 ^ ((hst->evals - 1) & 1)) : 0;
@@ -1301,11 +1375,7 @@ hs_status hs_solve_stress(hs_ctx* c, const double S[6], double tol, int max_iter
 
 // captured chunks hold kernel arguments: drop them when an argument changes
 static void drop_graphs(hs_ctx* c) {
-  for (int i = 0; i < 2; ++i) {
-    if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
-    c->gexec[i] = nullptr;
-    c->gchunks[i] = 0;
-  }
+  for (int i = 0; i < 2; ++i) drop_graph(c, i, true);
 }
 
 hs_status hs_set_eigenstrain(hs_ctx* c, const double* eps0) {
@@ -1520,6 +1590,10 @@ hs_status hs_profile_read(hs_ctx* c, double ms[HS_K_COUNT], long long launches[H
   }
   c->ev_used.clear();
   for (int k = 0; k < HS_K_COUNT; ++k) {
+    ms[k] += c->prof_ms[k];
+    c->prof_ms[k] = 0;
+  }
+  for (int k = 0; k < HS_K_COUNT; ++k) {
     launches[k] = c->launches[k];
     c->launches[k] = 0;
   }
@@ -1532,9 +1606,8 @@ void hs_destroy(hs_ctx* c) {
     cudaEventDestroy(ev.a);
     cudaEventDestroy(ev.b);
   }
+  for (int i = 0; i < 2; ++i) drop_graph(c, i, true);  // returns the graphs' events to the pool
   for (auto e : c->ev_pool) cudaEventDestroy(e);
-  for (auto& g : c->gexec)
-    if (g) cudaGraphExecDestroy(g);
   delete c;
 }
 

@@ -274,13 +274,41 @@ def test_graph_replay_matches_plain_launches(hs, prec):
         runs.append(res)
         counted.append(sum(n for _, n in s.profile_read().values()))
         s.close()
-    # replayed chunks are not counted as launches: fewer counted launches with graphs
-    assert counted[1] < counted[0]
+    # every replayed kernel is counted once per replay: the same launches either way
+    assert counted[1] == counted[0]
     for a, b in zip(*runs):
         assert a[0] == b[0] and a[1] == b[1]
         np.testing.assert_array_equal(a[2], b[2])
         np.testing.assert_array_equal(a[3], b[3])
         np.testing.assert_array_equal(a[4], b[4])
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_profiled_graph_replay_counts_and_times_every_kernel(hs, prec):
+    """With profiling on, replayed chunks carry the per-kernel events: the same launches per
+    kernel class as plain launches, a time for every class that ran, and the same results."""
+    grid = (64, 48, 36)
+    ids = synth.random_phase_map(grid, 2, seed=8)
+    table = synth.two_phase_table(1.0, 0.3, 20.0, 0.3)
+    stream = torch.cuda.Stream()
+    prof, res = [], []
+    for graphs in (0, 1):
+        s = hs.Solver(ids, table, precision=prec, check_every=4, use_graphs=graphs, stream=stream)
+        s.solve(E11, tol=0.0, max_iter=12, fields=False)  # first chunks: capture happens here
+        s.profile_read()
+        s.profile(True)
+        out = s.solve(E_MIX, tol=0.0, max_iter=40)
+        prof.append(s.profile_read())
+        res.append((out["iters"], out["err"], out["sig_eff"].copy(), s.err_history().copy()))
+        s.close()
+    for k in prof[0]:
+        assert prof[1][k][1] == prof[0][k][1], (k, prof[0][k], prof[1][k])
+        if prof[0][k][1]:
+            assert prof[1][k][0] > 0.0, (k, prof[1][k])
+            assert 0.25 < prof[1][k][0] / prof[0][k][0] < 4.0, (k, prof[0][k], prof[1][k])
+    assert res[0][0] == res[1][0] and res[0][1] == res[1][1]
+    np.testing.assert_array_equal(res[0][2], res[1][2])
+    np.testing.assert_array_equal(res[0][3], res[1][3])
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 2e-5)])
