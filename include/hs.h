@@ -81,8 +81,7 @@ typedef struct {
                            or 384 (FP64) */
   int use_graphs;       /* 1 (default): after its first chunk, a solve replays its iteration chunks
                            (check_every iterations) as one captured CUDA graph; 0: plain launches.
-                           With profiling on (hs_profile_enable) the captured chunk also records the
-                           per-kernel events, read back after each replay. */
+                           Chunks that profiling times (hs_profile_enable) run as plain launches. */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
@@ -198,14 +197,19 @@ enum {
   HS_K_COUNT = 10
 };
 
-/* Start (on != 0) or stop per-launch timing: every kernel launch of this context is then
- * bracketed by CUDA events on the context's stream and counted by class.  Timing adds a few
- * microseconds of host work per launch and no device work. */
+/* Start (on >= 1) or stop (on = 0) per-launch timing.  Timed launches are bracketed by CUDA
+ * events on the context's stream.  on = n times the launches of one iteration chunk in every n
+ * (as plain launches; the other chunks replay their captured graph as without timing) and every
+ * launch outside the chunks (FP64 sweeps, field passes, set-up); on = 1 times every launch.  The
+ * events add a few microseconds of host work and a short gap on the device per timed launch.
+ * Errors: HS_ERR_INVALID_ARG for on < 0. */
 hs_status hs_profile_enable(hs_ctx* c, int on);
 
-/* Accumulated device time (ms, from the events) and launch counts per kernel class since the
- * last read or enable; resets the accumulators.  ms and launches have HS_K_COUNT entries.
- * Launch counts are kept whether or not timing is enabled. */
+/* Device time (ms, from the events) and launch counts per kernel class since the last read;
+ * resets the accumulators.  ms and launches have HS_K_COUNT entries.  Launch counts cover every
+ * kernel launched or replayed, whether or not timing is enabled; when only some launches of a
+ * class were timed, ms is their total scaled by (launches / timed launches), so ms / launches is
+ * the mean time of the timed launches. */
 hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
 
 /* Limits of hs_residual_noalloc's fixed scratch array. */

@@ -223,11 +223,9 @@ struct hs_ctx {
   // captured iteration chunks: [0] full problem, [1] correction solves (refined)
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   int gchunks[2] = {0, 0};   // uncaptured chunks run so far (capture follows the first)
-  bool gexec_prof[2] = {false, false};       // the captured chunk records profiling events
   long long glaunches[2][HS_K_COUNT] = {};  // kernel launches per replay, by class
   bool capturing = false;                    // inside the stream capture of chunk cap_gi
   int cap_gi = 0;
-  bool gprof_ok = true;                      // event timing of replayed chunks works here
   bool dev_macro = false;    // plain modes under applied stress: E lives in the device status
   double Einit[6] = {0, 0, 0, 0, 0, 0};
   FftPlan plan[3];
@@ -252,8 +250,10 @@ struct hs_ctx {
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> ev_used;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<Ev> gev[2];            // events recorded by the nodes of captured chunk [gi]
-  double prof_ms[HS_K_COUNT] = {};   // kernel time of replayed chunks, read after each replay
+  int prof_every = 1;                // kernel events in one iteration chunk of every prof_every
+  bool prof_skip = false;            // this chunk records no kernel events
+  long long chunk_seq = 0;           // iteration chunks run with profiling on
+  long long timed[HS_K_COUNT] = {};  // launches that recorded events, by class
 };
 
 namespace {
@@ -269,8 +269,8 @@ hs_status cuda_fail(hs_ctx* c, cudaError_t e, const char* where) {
 }
 
 // Bracket one kernel launch: count it and, when profiling, record events.  Inside
-// the stream capture of an iteration chunk the launch is counted per replay and
-// the events become event-record nodes of the graph, read after each replay.
+// the stream capture of an iteration chunk the launch is counted once per replay
+// instead, and records no events (a profiled chunk runs as plain launches).
 struct LaunchScope {
   hs_ctx* c;
   int kind;
@@ -278,15 +278,11 @@ struct LaunchScope {
   LaunchScope(hs_ctx* c_, int kind_) : c(c_), kind(kind_) {
     if (c->capturing) c->glaunches[c->cap_gi][kind]++;
     else c->launches[kind]++;
-    if (c->prof) {
+    if (c->prof && !c->capturing && !c->prof_skip) {
       a = take();
       b = take();
-      if (a) record(a);
+      if (a) cudaEventRecord(a, c->stream);
     }
-  }
-  void record(cudaEvent_t e) {
-    if (c->capturing) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
-    else cudaEventRecord(e, c->stream);
   }
   cudaEvent_t take() {
     cudaEvent_t e = nullptr;
@@ -300,8 +296,9 @@ struct LaunchScope {
   }
   ~LaunchScope() {
     if (a && b) {
-      record(b);
-      (c->capturing ? c->gev[c->cap_gi] : c->ev_used).push_back({kind, a, b});
+      cudaEventRecord(b, c->stream);
+      c->ev_used.push_back({kind, a, b});
+      c->timed[kind]++;
     } else {
       if (a) c->ev_pool.push_back(a);
       if (b) c->ev_pool.push_back(b);
@@ -309,35 +306,24 @@ struct LaunchScope {
   }
 };
 
-// Forget captured chunk gi: its graph, its profiling events and its launch counts.
+// Forget captured chunk gi: its graph and its launch counts.
 void drop_graph(hs_ctx* c, int gi, bool reset_chunks) {
   if (c->gexec[gi]) cudaGraphExecDestroy(c->gexec[gi]);
   c->gexec[gi] = nullptr;
-  c->gexec_prof[gi] = false;
-  for (auto& ev : c->gev[gi]) {
-    c->ev_pool.push_back(ev.a);
-    c->ev_pool.push_back(ev.b);
-  }
-  c->gev[gi].clear();
   for (int k = 0; k < HS_K_COUNT; ++k) c->glaunches[gi][k] = 0;
   if (reset_chunks) c->gchunks[gi] = 0;
 }
 
-// After a replay of chunk gi has completed (the stream was synchronised): count its
-// launches and add the times its event nodes recorded.
+// A replay of chunk gi was enqueued: count its kernel launches.
 void account_replay(hs_ctx* c, int gi) {
   for (int k = 0; k < HS_K_COUNT; ++k) c->launches[k] += c->glaunches[gi][k];
-  if (!c->gexec_prof[gi]) return;
-  for (auto& ev : c->gev[gi]) {
-    float t = 0;
-    if (cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess) {
-      c->prof_ms[ev.kind] += t;
-    } else {
-      cudaGetLastError();
-      c->gprof_ok = false;  // profile with plain launches from now on
-    }
-  }
 }
+
+// Clears the per-chunk profiling switch on every exit from the iteration loop.
+struct ChunkProfGuard {
+  hs_ctx* c;
+  ~ChunkProfGuard() { c->prof_skip = false; }
+};
 
 #define HS_CU(c, call)                                    \
   do {                                                    \
@@ -608,35 +594,26 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
   int cur = cur0;
   const int chunk = std::max(1, c->opt.check_every);
   // the legacy default stream cannot be captured: plain launches there
-  const bool graphs = c->opt.use_graphs && !(c->prof && !c->gprof_ok) && !c->xfuse && c->stream != nullptr &&
-                      c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
+  const bool graphs = c->opt.use_graphs && !c->xfuse && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+                      c->stream != cudaStreamPerThread;
   const int gi = (src != nullptr) ? 1 : 0;
-  // a chunk captured with profiling on or off is recaptured when that changes
-  if (c->gexec[gi] != nullptr && c->gexec_prof[gi] != c->prof) drop_graph(c, gi, false);
+  ChunkProfGuard guard{c};
   for (;;) {
-    if (graphs && c->gexec[gi] != nullptr) {
+    // profiling: one chunk in prof_every runs as plain launches that record kernel events;
+    // the others run as they would without profiling
+    const bool sampled = c->prof && (c->chunk_seq++ % c->prof_every) == 0;
+    c->prof_skip = c->prof && !sampled;
+    if (graphs && !sampled && c->gexec[gi] != nullptr) {
       HS_CU(c, cudaGraphLaunch(c->gexec[gi], c->stream));
+      account_replay(c, gi);
       hs_status s = read_status(c, hst);
       if (s != HS_OK) return s;
-      account_replay(c, gi);
       if (hst->done) break;
       continue;
     }
-    bool capture = graphs && c->gchunks[gi] >= 1;
+    bool capture = graphs && !sampled && c->gchunks[gi] >= 1;
     if (capture) {
       drop_graph(c, gi, false);
-      if (c->prof) {
-        // the capture's event nodes take their events from the pool: two per launch, at most
-        // six launches per iteration; created here, outside the capture
-        while (c->ev_pool.size() < (size_t)12 * chunk) {
-          cudaEvent_t ev = nullptr;
-          if (cudaEventCreate(&ev) != cudaSuccess) {
-            cudaGetLastError();
-            break;
-          }
-          c->ev_pool.push_back(ev);
-        }
-      }
       if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         // a stream that refuses capture (e.g. one already being captured): plain launches from now on
         cudaGetLastError();
@@ -686,13 +663,12 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
         return cuda_fail(c, e, "graph capture");
       }
       c->gexec[gi] = ex;
-      c->gexec_prof[gi] = c->prof;
       HS_CU(c, cudaGraphLaunch(ex, c->stream));
+      account_replay(c, gi);
     }
     ++c->gchunks[gi];
     hs_status s = read_status(c, hst);
     if (s != HS_OK) return s;
-    if (capture) account_replay(c, gi);
     if (hst->done) break;
   }
   *last_in = c->xfuse ? (cur0 ^ ((hst->evals - 1) & 1)) : 0;
@@ -1572,8 +1548,10 @@ hs_status hs_get_reference_medium(const hs_ctx* c, double C0[36]) {
 }
 
 hs_status hs_profile_enable(hs_ctx* c, int on) {
-  if (!c) return HS_ERR_INVALID_ARG;
+  if (!c || on < 0) return HS_ERR_INVALID_ARG;
   c->prof = (on != 0);
+  c->prof_every = on > 0 ? on : 1;
+  c->chunk_seq = 0;
   return HS_OK;
 }
 
@@ -1590,12 +1568,11 @@ hs_status hs_profile_read(hs_ctx* c, double ms[HS_K_COUNT], long long launches[H
   }
   c->ev_used.clear();
   for (int k = 0; k < HS_K_COUNT; ++k) {
-    ms[k] += c->prof_ms[k];
-    c->prof_ms[k] = 0;
-  }
-  for (int k = 0; k < HS_K_COUNT; ++k) {
+    // sampled profiling: the timed launches' total, scaled to all launches of the class
+    if (c->timed[k] > 0 && c->timed[k] < c->launches[k]) ms[k] *= (double)c->launches[k] / (double)c->timed[k];
     launches[k] = c->launches[k];
     c->launches[k] = 0;
+    c->timed[k] = 0;
   }
   return HS_OK;
 }

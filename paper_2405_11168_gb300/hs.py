@@ -327,6 +327,7 @@ class Solver:
         return out.reshape(6, 6)
 
     def profile(self, on=True):
+        """Start timing (True, or n: one iteration chunk in n) or stop it (False / 0)."""
         _check(self.lib, self.lib.hs_profile_enable(self.ctx, int(on)), self.ctx)
 
     def profile_read(self):

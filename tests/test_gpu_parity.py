@@ -284,9 +284,10 @@ def test_graph_replay_matches_plain_launches(hs, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-def test_profiled_graph_replay_counts_and_times_every_kernel(hs, prec):
-    """With profiling on, replayed chunks carry the per-kernel events: the same launches per
-    kernel class as plain launches, a time for every class that ran, and the same results."""
+def test_sampled_profiling_over_graph_replay(hs, prec):
+    """Profiling that times one iteration chunk in three (the others replay their graph)
+    reports the same launches per kernel class as timing every plain launch, a mean time
+    per launch close to it for every class that ran, and leaves the results unchanged."""
     grid = (64, 48, 36)
     ids = synth.random_phase_map(grid, 2, seed=8)
     table = synth.two_phase_table(1.0, 0.3, 20.0, 0.3)
@@ -296,7 +297,7 @@ def test_profiled_graph_replay_counts_and_times_every_kernel(hs, prec):
         s = hs.Solver(ids, table, precision=prec, check_every=4, use_graphs=graphs, stream=stream)
         s.solve(E11, tol=0.0, max_iter=12, fields=False)  # first chunks: capture happens here
         s.profile_read()
-        s.profile(True)
+        s.profile(3 if graphs else 1)
         out = s.solve(E_MIX, tol=0.0, max_iter=40)
         prof.append(s.profile_read())
         res.append((out["iters"], out["err"], out["sig_eff"].copy(), s.err_history().copy()))
