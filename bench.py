@@ -577,7 +577,9 @@ TORCH_ITERS = 10
 # Kernel times in the timed region come from CUDA events on one iteration chunk
 # in PROFILE_EVERY (run as plain launches) and on every launch outside the
 # chunks; the other chunks replay their CUDA graph as an untimed solve does.
-PROFILE_EVERY = 4
+# A solve here runs 8 chunks, so a period of 5 moves the timed chunk through
+# every position in a solve instead of always timing the same ones.
+PROFILE_EVERY = 5
 
 # FP64 operations per voxel of the real-space residual sweep (isotropic phases):
 # 2 tetrahedra x (gradient 3x6 adds + 3 x 3 scalings + 9 adds/doublings for the
