@@ -100,8 +100,18 @@ class Server:
             t.start()
             self._workers.append(t)
 
+    def request_bytes(self, req: Request) -> int:
+        """Device bytes the request holds while it runs (admission uses this)."""
+        return request_bytes(req)
+
+    def _start_slot(self):
+        """Per-worker set-up: the device and the worker's own stream."""
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        return torch.cuda.Stream(self.device)
+
     def submit(self, req: Request) -> Future:
-        need = request_bytes(req)
+        need = self.request_bytes(req)
         if need > self.budget:
             raise ValueError(f"request needs {need} bytes, above the budget of {self.budget}")
         fut = Future()
@@ -154,8 +164,7 @@ class Server:
     def _worker(self):
         torch = self.torch
         try:
-            torch.cuda.set_device(self.device)
-            stream = torch.cuda.Stream(self.device)
+            stream = self._start_slot()
         except BaseException as e:  # noqa: BLE001 - a slot that cannot start fails the queue, not silently
             self._fail_pending(e)
             return
@@ -166,9 +175,12 @@ class Server:
             req, need, fut = item
             t_start = time.perf_counter()
             try:
-                with torch.cuda.stream(stream):
+                if stream is not None:
+                    with torch.cuda.stream(stream):
+                        res = self._run(req, stream)
+                    stream.synchronize()
+                else:
                     res = self._run(req, stream)
-                stream.synchronize()
                 res.queued_s = t_start - req.arrival
                 res.latency_s = time.perf_counter() - req.arrival
                 res.bytes = need
