@@ -49,17 +49,37 @@ typedef enum {
 } hs_status;
 
 enum { HS_FP64 = 0, HS_FP32 = 1, HS_FP32_REFINED = 2 };
-enum { HS_IDS_U8 = 0, HS_IDS_U16 = 1 };
+enum { HS_IDS_U8 = 0, HS_IDS_U16 = 1, HS_COEFFS_F32 = 2 };
+#define HS_MAX_PHASES 65536
 
-/* Microstructure: a phase id per voxel and a stiffness per phase
- * (lambda(r) of Eq. linear_elasticity, with eps0 = 0). */
+/* Microstructure: the stiffness field lambda(r) of Eq. linear_elasticity, either as a phase id per
+ * voxel with a stiffness per phase (HS_IDS_U8 / HS_IDS_U16), or as the full 6x6 stiffness of every
+ * voxel (HS_COEFFS_F32).  hs_create stores the per-voxel form exactly as phases: voxels whose 21
+ * coefficients are identical share a phase (see hs_compress_coefficients), so a field with more
+ * than HS_MAX_PHASES distinct stiffnesses is refused with HS_ERR_UNSUPPORTED_SIZE. */
 typedef struct {
-  int kind;             /* HS_IDS_U8 or HS_IDS_U16 */
-  const void* ids;      /* [N3][N2][N1] phase ids; host or device pointer, read during hs_create only */
-  const double* table;  /* host pointer, nphase x 36: row-major 6x6 Voigt stiffness per phase;
-                           must be symmetric with a non-negative diagonal (C = 0 is a void) */
-  int nphase;           /* 1..65536; every id must be < nphase */
+  int kind;             /* HS_IDS_U8, HS_IDS_U16 or HS_COEFFS_F32 */
+  const void* ids;      /* ids kinds: [N3][N2][N1] phase ids; host or device pointer, read during hs_create
+                           only.  HS_COEFFS_F32: unused (NULL) */
+  const double* table;  /* ids kinds: host pointer, nphase x 36: row-major 6x6 Voigt stiffness per phase;
+                           must be symmetric with a non-negative diagonal (C = 0 is a void).
+                           HS_COEFFS_F32: unused (NULL) */
+  int nphase;           /* ids kinds: 1..HS_MAX_PHASES; every id must be < nphase.  HS_COEFFS_F32: unused */
+  const float* coeffs;  /* HS_COEFFS_F32: [21][N3][N2][N1], the upper triangle of each voxel's 6x6 Voigt
+                           stiffness in row order (C11 C12 .. C16 C22 .. C26 .. C66), host or device
+                           pointer, read during hs_create only; size the workspace with
+                           nphase = HS_MAX_PHASES.  Other kinds: unused */
 } hs_material;
+
+/* Exact compression of a per-voxel stiffness field (host only; needs no GPU): voxels whose 21
+ * coefficients are bit-identical (-0 read as +0) share a phase, numbered in order of first
+ * appearance with x fastest.  coeffs: host [21][N3][N2][N1] as hs_material.coeffs; ids: host
+ * [N3][N2][N1] output; table: host output, room for `capacity` phases x 36 (symmetric 6x6, the
+ * FP32 coefficients widened to FP64); *nphase: phases found.
+ * Errors: HS_ERR_INVALID_ARG (null pointer, grid entry < 1, capacity < 1, non-finite coefficient),
+ * HS_ERR_UNSUPPORTED_SIZE (more than capacity distinct stiffnesses). */
+hs_status hs_compress_coefficients(const int grid[3], const float* coeffs, unsigned short* ids, double* table,
+                                   int capacity, int* nphase);
 
 typedef struct {
   int precision;        /* HS_FP64, HS_FP32 or HS_FP32_REFINED */

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/hs.h"
@@ -330,6 +331,130 @@ struct ChunkProfGuard {
     cudaError_t _e = (call);                              \
     if (_e != cudaSuccess) return cuda_fail(c, _e, #call); \
   } while (0)
+
+// Exact compression of a per-voxel stiffness field into phase ids and a phase
+// table: voxels whose 21 coefficients are bit-identical (-0 read as +0) share a
+// phase, numbered in order of first appearance.  Voxels are fed in memory order
+// (x fastest), a run of planes at a time.
+class CoeffCompressor {
+ public:
+  CoeffCompressor(size_t nvox, int capacity) : ids(nvox), cap_(capacity) {}
+  // comp[c] points at coefficient c of `count` consecutive voxels starting at voxel `base`
+  hs_status add(const float* const comp[21], size_t count, size_t base) {
+    for (size_t v = 0; v < count; ++v) {
+      Key k;
+      for (int c = 0; c < 21; ++c) {
+        float f = comp[c][v];
+        if (!std::isfinite(f)) return HS_ERR_INVALID_ARG;
+        if (f == 0.0f) f = 0.0f;  // -0 and +0 are the same stiffness
+        memcpy(&k.w[c], &f, 4);
+      }
+      int id;
+      if (prev_id_ >= 0 && k == prev_) {
+        id = prev_id_;  // fast path: grains are runs along x
+      } else {
+        auto it = index_.find(k);
+        if (it != index_.end()) {
+          id = it->second;
+        } else {
+          if ((int)index_.size() >= cap_) return HS_ERR_UNSUPPORTED_SIZE;
+          id = (int)index_.size();
+          index_.emplace(k, id);
+          table.resize(table.size() + 36);
+          double* C = &table[(size_t)id * 36];
+          int t = 0;
+          for (int i = 0; i < 6; ++i)
+            for (int j = i; j < 6; ++j) {
+              float f;
+              memcpy(&f, &k.w[t++], 4);
+              C[i * 6 + j] = C[j * 6 + i] = (double)f;
+            }
+        }
+      }
+      ids[base + v] = (uint16_t)id;
+      prev_ = k;
+      prev_id_ = id;
+    }
+    return HS_OK;
+  }
+  int nphase() const { return (int)index_.size(); }
+  std::vector<uint16_t> ids;
+  std::vector<double> table;
+
+ private:
+  struct Key {
+    uint32_t w[21];
+    bool operator==(const Key& o) const { return memcmp(w, o.w, sizeof(w)) == 0; }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      uint64_t h = 1469598103934665603ull;  // FNV-1a over the coefficient bits
+      for (int i = 0; i < 21; ++i) {
+        h ^= k.w[i];
+        h *= 1099511628211ull;
+      }
+      return (size_t)h;
+    }
+  };
+  std::unordered_map<Key, int, KeyHash> index_;
+  Key prev_{};
+  int prev_id_ = -1;
+  int cap_;
+};
+
+// A material in ids form: kind HS_COEFFS_F32 is compressed (its coefficients read
+// from host or device memory a z plane at a time); other kinds pass through.
+struct IdsMaterial {
+  std::vector<uint16_t> ids;
+  std::vector<double> table;
+  hs_material m{};
+  const hs_material* use = nullptr;
+};
+
+hs_status to_ids_material(const hs_material* in, const int grid[3], void* stream, IdsMaterial* out) {
+  if (in->kind != HS_COEFFS_F32) {
+    out->use = in;
+    return HS_OK;
+  }
+  if (!in->coeffs) return HS_ERR_INVALID_ARG;
+  const size_t plane = (size_t)grid[0] * grid[1], N = plane * grid[2];
+  CoeffCompressor cc(N, HS_MAX_PHASES);
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, in->coeffs);
+  const bool dev_ptr = (e == cudaSuccess) && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+  if (e != cudaSuccess) cudaGetLastError();
+  const float* comp[21];
+  if (!dev_ptr) {
+    for (int c = 0; c < 21; ++c) comp[c] = in->coeffs + (size_t)c * N;
+    hs_status s = cc.add(comp, N, 0);
+    if (s != HS_OK) return s;
+  } else {
+    std::vector<float> buf(21 * plane);
+    for (int c = 0; c < 21; ++c) comp[c] = buf.data() + (size_t)c * plane;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int z = 0; z < grid[2]; ++z) {
+      // the 21 coefficient planes of z: one strided copy
+      e = cudaMemcpy2DAsync(buf.data(), plane * 4, in->coeffs + (size_t)z * plane, N * 4, plane * 4, 21,
+                            cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        g_last_error = std::string("coefficient read: ") + cudaGetErrorString(e);
+        return HS_ERR_CUDA;
+      }
+      hs_status s = cc.add(comp, plane, (size_t)z * plane);
+      if (s != HS_OK) return s;
+    }
+  }
+  out->ids = std::move(cc.ids);
+  out->table = std::move(cc.table);
+  out->m.kind = HS_IDS_U16;
+  out->m.ids = out->ids.data();
+  out->m.table = out->table.data();
+  out->m.nphase = cc.nphase();
+  out->m.coeffs = nullptr;
+  out->use = &out->m;
+  return HS_OK;
+}
 
 hs_status check_grid(const int grid[3]) {
   for (int i = 0; i < 3; ++i) {
@@ -932,11 +1057,24 @@ hs_status hs_workspace_size(const int grid[3], int nphase, const hs_options* opt
   return HS_OK;
 }
 
-hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const double C0[36],
+hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, const double C0[36],
                     const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
-  if (!out || !grid || !m || !m->ids || !m->table || !workspace)
-    return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
+  if (!out || !grid || !m_in || !workspace) return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  if (m_in->kind == HS_COEFFS_F32) {
+    hs_status sg = check_grid(grid);
+    if (sg != HS_OK) return fail(nullptr, sg, "unsupported grid size");
+  }
+  IdsMaterial im;
+  {
+    hs_status sm = to_ids_material(m_in, grid, stream, &im);
+    if (sm == HS_ERR_CUDA) return fail(nullptr, sm, g_last_error);
+    if (sm == HS_ERR_UNSUPPORTED_SIZE)
+      return fail(nullptr, sm, "more than HS_MAX_PHASES distinct stiffnesses in the per-voxel field");
+    if (sm != HS_OK) return fail(nullptr, sm, "bad per-voxel stiffness field (null or non-finite)");
+  }
+  const hs_material* m = im.use;
+  if (!m->ids || !m->table) return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
   hs_options o;
   hs_default_options(&o);
   if (opt) o = *opt;
@@ -947,10 +1085,10 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
       (o.use_graphs != 0 && o.use_graphs != 1))
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
-  if (m->nphase < 1 || m->nphase > 65536)
+  if (m->nphase < 1 || m->nphase > HS_MAX_PHASES)
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad nphase");
   hs_status s = check_grid(grid);
-  if (s != HS_OK) return fail(nullptr, s, "unsupported grid size (even, 4..512, factors 2 and 3)");
+  if (s != HS_OK) return fail(nullptr, s, "unsupported grid size (even, 4..512, prime factors 2, 3, 5, 7, 11)");
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
     return fail(nullptr, HS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   // material table checks
@@ -1451,9 +1589,18 @@ bool table_isotropic(const double* table, int nphase) {
 }
 }  // namespace
 
-hs_status hs_autotune(const int grid[3], const hs_material* m, const hs_options* base, void* workspace,
+hs_status hs_autotune(const int grid[3], const hs_material* m_in, const hs_options* base, void* workspace,
                       size_t workspace_bytes, void* stream, int iters, hs_options* best, double* best_ms) {
-  if (!grid || !m || !m->table || !best || iters < 1) return fail(nullptr, HS_ERR_INVALID_ARG, "bad argument");
+  if (!grid || !m_in || !best || iters < 1) return fail(nullptr, HS_ERR_INVALID_ARG, "bad argument");
+  IdsMaterial im;
+  if (m_in->kind == HS_COEFFS_F32 && check_grid(grid) != HS_OK)
+    return fail(nullptr, HS_ERR_UNSUPPORTED_SIZE, "unsupported grid size");
+  {
+    hs_status sm = to_ids_material(m_in, grid, stream, &im);
+    if (sm != HS_OK) return fail(nullptr, sm, sm == HS_ERR_CUDA ? g_last_error : "bad per-voxel stiffness field");
+  }
+  const hs_material* m = im.use;
+  if (!m->table) return fail(nullptr, HS_ERR_INVALID_ARG, "bad argument");
   hs_options b;
   hs_default_options(&b);
   if (base) b = *base;
@@ -1574,6 +1721,25 @@ hs_status hs_profile_read(hs_ctx* c, double ms[HS_K_COUNT], long long launches[H
     c->launches[k] = 0;
     c->timed[k] = 0;
   }
+  return HS_OK;
+}
+
+hs_status hs_compress_coefficients(const int grid[3], const float* coeffs, unsigned short* ids, double* table,
+                                   int capacity, int* nphase) {
+  if (!grid || !coeffs || !ids || !table || !nphase || capacity < 1)
+    return fail(nullptr, HS_ERR_INVALID_ARG, "null argument or capacity < 1");
+  for (int i = 0; i < 3; ++i)
+    if (grid[i] < 1) return fail(nullptr, HS_ERR_INVALID_ARG, "grid entry < 1");
+  const size_t N = (size_t)grid[0] * grid[1] * grid[2];
+  CoeffCompressor cc(N, capacity);
+  const float* comp[21];
+  for (int c = 0; c < 21; ++c) comp[c] = coeffs + (size_t)c * N;
+  hs_status s = cc.add(comp, N, 0);
+  if (s == HS_ERR_UNSUPPORTED_SIZE) return fail(nullptr, s, "more distinct stiffnesses than capacity");
+  if (s != HS_OK) return fail(nullptr, s, "non-finite coefficient");
+  memcpy(ids, cc.ids.data(), N * sizeof(uint16_t));
+  memcpy(table, cc.table.data(), cc.table.size() * sizeof(double));
+  *nphase = cc.nphase();
   return HS_OK;
 }
 

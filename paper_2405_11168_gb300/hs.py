@@ -29,7 +29,8 @@ HS_ERR_TIMEOUT = -6
 
 HS_FP64, HS_FP32, HS_FP32_REFINED = 0, 1, 2
 KERNEL_CLASSES = ["xpass", "y_fwd", "z_green", "y_inv", "resid64", "fields", "other", "x_inv", "x_fwd", "xpass_src"]
-HS_IDS_U8, HS_IDS_U16 = 0, 1
+HS_IDS_U8, HS_IDS_U16, HS_COEFFS_F32 = 0, 1, 2
+HS_MAX_PHASES = 65536
 
 # every exported function of include/hs.h
 EXPORTS = [
@@ -47,6 +48,7 @@ EXPORTS = [
     "hs_profile_enable",
     "hs_profile_read",
     "hs_residual_noalloc",
+    "hs_compress_coefficients",
     "hs_destroy",
     "hs_error_string",
     "hs_last_error",
@@ -55,7 +57,8 @@ EXPORTS = [
 
 class hs_material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ids", ctypes.c_void_p),
-                ("table", ctypes.POINTER(ctypes.c_double)), ("nphase", ctypes.c_int)]
+                ("table", ctypes.POINTER(ctypes.c_double)), ("nphase", ctypes.c_int),
+                ("coeffs", ctypes.c_void_p)]
 
 
 class hs_options(ctypes.Structure):
@@ -105,6 +108,7 @@ def load(path: str = LIB_PATH):
     lib.hs_profile_enable.argtypes = [P, I]
     lib.hs_profile_read.argtypes = [P, dptr, ctypes.POINTER(ctypes.c_longlong)]
     lib.hs_residual_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), P, dptr, I, dptr, P, P, dptr, dptr, P]
+    lib.hs_compress_coefficients.argtypes = [ctypes.POINTER(ctypes.c_int), P, P, dptr, I, iptr]
     lib.hs_destroy.argtypes = [P]
     lib.hs_destroy.restype = None
     lib.hs_error_string.argtypes = [I]
@@ -169,6 +173,31 @@ def workspace_size(grid, nphase, opt):
 OPTION_FIELDS = [f for f, _ in hs_options._fields_]
 
 
+def upper_triangle(C):
+    """The 21 upper-triangle entries of 6x6 stiffness matrices (..., 6, 6), in the row order of
+    hs_material.coeffs (C11 C12 .. C16 C22 .. C66)."""
+    C = np.asarray(C)
+    iu = np.triu_indices(6)
+    return C[..., iu[0], iu[1]]
+
+
+def compress_coefficients(coeffs, capacity=HS_MAX_PHASES):
+    """hs_compress_coefficients on a host array [21][N3][N2][N1]: (ids uint16 [N3][N2][N1],
+    table [nphase, 6, 6]), exact (voxels with identical coefficients share a phase)."""
+    lib = load()
+    c = np.ascontiguousarray(coeffs, dtype=np.float32)
+    if c.ndim != 4 or c.shape[0] != 21:
+        raise ValueError(f"coefficients must be [21][N3][N2][N1], got {c.shape}")
+    n3, n2, n1 = c.shape[1:]
+    ids = np.empty((n3, n2, n1), dtype=np.uint16)
+    table = np.empty((capacity, 36))
+    n = ctypes.c_int()
+    g = (ctypes.c_int * 3)(n1, n2, n3)
+    _check(lib, lib.hs_compress_coefficients(g, c.ctypes.data, ids.ctypes.data, _dp(table), int(capacity),
+                                             ctypes.byref(n)))
+    return ids, table[: n.value].reshape(-1, 6, 6).copy()
+
+
 def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None, **optkw):
     """hs_autotune on a device copy of ``ids``; returns (options dict, ms per evaluation or -1 if cached)."""
     import torch
@@ -183,7 +212,7 @@ def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None,
     nbytes = workspace_size(grid, table.shape[0], base)
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=ids_t.device)
     ptr = (ws.data_ptr() + 255) & ~255
-    m = hs_material(kind, ctypes.c_void_p(ids_t.data_ptr()), _dp(table), table.shape[0])
+    m = hs_material(kind, ctypes.c_void_p(ids_t.data_ptr()), _dp(table), table.shape[0], None)
     st = stream if stream is not None else torch.cuda.current_stream(ids_t.device)
     st.wait_stream(torch.cuda.current_stream(ids_t.device))
     best = hs_options()
@@ -198,24 +227,47 @@ def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None,
 class Solver:
     """One microstructure on one device (thin wrapper over hs_create / hs_solve)."""
 
-    def __init__(self, ids, table, C0=None, precision=HS_FP64, device="cuda", stream=None, **optkw):
+    def __init__(self, ids, table, C0=None, precision=HS_FP64, device="cuda", stream=None, coeffs=None, **optkw):
+        """ids [N3][N2][N1] and table [nphase][6][6]; or ids = table = None and ``coeffs``, the full
+        stiffness of every voxel as [21][N3][N2][N1] float32 (upper triangles, host array or
+        device tensor), which the library stores exactly as phases."""
         import torch
 
         self.lib = load()
         self.torch = torch
+        if coeffs is not None:
+            shape = tuple(coeffs.shape[1:])
+        else:
+            shape = tuple(ids.shape)
         ids_t = ids if isinstance(ids, torch.Tensor) else None
-        shape = tuple(ids.shape)
         self.grid = (shape[2], shape[1], shape[0])
         self.N = int(np.prod(shape))
-        table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
-        self.nphase = table.shape[0]
         self.opt = default_options(precision=precision, **optkw)
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        if coeffs is not None:
+            table = np.zeros((1, 6, 6))
+            self.nphase = HS_MAX_PHASES  # workspace for the largest phase count the field may hold
+        else:
+            table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
+            self.nphase = table.shape[0]
         nbytes = workspace_size(self.grid, self.nphase, self.opt)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) & ~255
-        if ids_t is None:
+        if coeffs is not None:
+            if isinstance(coeffs, torch.Tensor):
+                ct = coeffs.to(dtype=torch.float32).contiguous()
+                self.stream.wait_stream(torch.cuda.current_stream(ct.device) if ct.is_cuda
+                                        else torch.cuda.current_stream(device))
+                cptr = ct.data_ptr()
+            else:
+                ct = np.ascontiguousarray(coeffs, dtype=np.float32)
+                cptr = ct.ctypes.data
+            if tuple(ct.shape)[0] != 21 or len(ct.shape) != 4:
+                raise ValueError(f"coefficients must be [21][N3][N2][N1], got {tuple(ct.shape)}")
+            self._ids_keep = ct
+            kind, ids_ptr = HS_COEFFS_F32, None
+        elif ids_t is None:
             # host ids: hs_create copies them to the device
             ids_np = np.ascontiguousarray(ids)
             if ids_np.ndim != 3 or ids_np.dtype.kind not in "iu":
@@ -236,7 +288,10 @@ class Solver:
             ids_ptr = ids_t.data_ptr()
             self._ids_keep = ids_t
         self._table = table
-        m = hs_material(kind, ctypes.c_void_p(ids_ptr), _dp(table), self.nphase)
+        if kind == HS_COEFFS_F32:
+            m = hs_material(kind, None, None, 0, ctypes.c_void_p(cptr))
+        else:
+            m = hs_material(kind, ctypes.c_void_p(ids_ptr), _dp(table), self.nphase, None)
         c0 = None if C0 is None else np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(36))
         self._c0 = c0
         ctx = ctypes.c_void_p()

@@ -120,3 +120,54 @@ def test_binding_normalises_phase_ids_for_the_c_abi():
         hs._ids_tensor(torch.zeros(2, 2, 2), cpu)
     with pytest.raises(ValueError):
         hs._ids_tensor(torch.zeros(4, 4, dtype=torch.uint8), cpu)
+
+
+def test_compress_coefficients_is_exact_and_ordered(lib):
+    """hs_compress_coefficients (host only) turns a per-voxel stiffness field into
+    phase ids and a table that reproduce every voxel's coefficients exactly, with
+    phases numbered by first appearance (x fastest), -0 read as +0, and refuses
+    non-finite fields or more stiffnesses than its capacity."""
+    from paper_2405_11168_gb300 import hs
+    import synth
+
+    grid = (12, 10, 8)
+    gids, _ = synth.voronoi_grains(grid, 7, seed=4)
+    rot = synth.polycrystal_table(168.4, 121.4, 75.4, synth.random_rotations(7, seed=5)).astype(np.float32)
+    coeffs = np.moveaxis(hs.upper_triangle(rot)[gids.astype(np.int64)], -1, 0).copy()  # [21][N3][N2][N1]
+    ids, table = hs.compress_coefficients(coeffs)
+    assert ids.dtype == np.uint16 and ids.shape == gids.shape
+    assert table.shape == (len(np.unique(gids)), 6, 6)
+    np.testing.assert_array_equal(np.moveaxis(hs.upper_triangle(table)[ids.astype(np.int64)], -1, 0),
+                                  coeffs.astype(np.float64))
+    np.testing.assert_array_equal(table, np.swapaxes(table, 1, 2))
+    first = [int(v) for v in dict.fromkeys(gids.reshape(-1).tolist())]  # grains in order of appearance
+    assert [int(ids.reshape(-1)[np.argmax(gids.reshape(-1) == g)]) for g in first] == list(range(len(first)))
+    # -0 and +0 are one stiffness
+    two = np.zeros((21, 1, 1, 2), dtype=np.float32)
+    two[0] = 1.0
+    two[1, 0, 0, 1] = -0.0
+    ids2, table2 = hs.compress_coefficients(two)
+    assert ids2.tolist() == [[[0, 0]]] and table2.shape == (1, 6, 6)
+    # capacity and finiteness
+    with pytest.raises(hs.HSError) as ei:
+        hs.compress_coefficients(coeffs, capacity=len(first) - 1)
+    assert ei.value.status == hs.HS_ERR_UNSUPPORTED_SIZE
+    bad = coeffs.copy()
+    bad[5, 1, 2, 3] = np.nan
+    with pytest.raises(hs.HSError) as ei:
+        hs.compress_coefficients(bad)
+    assert ei.value.status == hs.HS_ERR_INVALID_ARG
+
+
+def test_create_rejects_null_coefficient_field(lib):
+    from paper_2405_11168_gb300 import hs
+
+    g = (ctypes.c_int * 3)(8, 8, 8)
+    m = hs.hs_material(hs.HS_COEFFS_F32, None, None, 0, None)
+    ctx = ctypes.c_void_p()
+    o = hs.default_options()
+    ws = ctypes.create_string_buffer(512)
+    addr = (ctypes.addressof(ws) + 255) & ~255
+    st = lib.hs_create(ctypes.byref(ctx), g, ctypes.byref(m), None, ctypes.byref(o), ctypes.c_void_p(addr),
+                       ctypes.c_size_t(256), None)
+    assert st == hs.HS_ERR_INVALID_ARG
