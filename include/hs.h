@@ -149,6 +149,8 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const
  *             number of residual evaluations: a homogeneous medium converges in 1.
  *  eps_out, sig_out  device pointers [6][N3][N2][N1] (double, or float if opt.out_f32), or NULL:
  *             eps = E + 1/2(deps^T1 + deps^T2) (tensor components), sigma = 1/2(sigma^T1+sigma^T2).
+ *             The fields are written only when both pointers are given; with either NULL, neither
+ *             is written (and no field pass runs).
  *  sig_eff    host, 6: <sigma> in Voigt order (the effective stress).
  *  iters      host: residual evaluations used.   final_err: host: err of the last evaluation.
  * Starts from u = 0 unless hs_set_state was called since the last solve.
