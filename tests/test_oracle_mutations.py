@@ -112,3 +112,57 @@ def _mut_green_transpose(orig):
 def test_planted_mistake_is_caught(monkeypatch, name, factory):
     monkeypatch.setattr(T, name, factory(getattr(T, name)))
     assert not _pins_hold()
+
+
+# ---- the applied-stress loop (Section 2.5, Algorithm 1 step 6) --------------------------
+def _laminate_compliance_pin_holds():
+    """Stress control on a laminate reaches the closed-form compliance (inverse Backus
+    stiffness) applied to sigma^a."""
+    grid = (8, 4, 4)
+    layers = [0, 1, 1, 0, 0, 0, 1, 0]
+    ids = synth.laminate_x(grid, layers)
+    table = synth.two_phase_table(1.0, 0.3, 4.0, 0.25)
+    lam = np.array([t[0, 1] for t in table])
+    mu = np.array([t[3, 3] for t in table])
+    f = np.array([1 - np.mean(layers), np.mean(layers)])
+    a = lambda x: np.sum(f * x)  # noqa: E731
+    M = lam + 2 * mu
+    C = np.zeros((6, 6))
+    C[0, 0] = 1 / a(1 / M)
+    C[0, 1] = C[1, 0] = C[0, 2] = C[2, 0] = a(lam / M) / a(1 / M)
+    C[1, 1] = C[2, 2] = a(lam + 2 * mu - lam ** 2 / M) + a(lam / M) ** 2 / a(1 / M)
+    C[1, 2] = C[2, 1] = a(lam - lam ** 2 / M) + a(lam / M) ** 2 / a(1 / M)
+    C[3, 3] = a(mu)
+    C[4, 4] = C[5, 5] = 1 / a(1 / mu)
+    sa_v = np.array([0.2, -0.05, 0.1, 0.03, -0.02, 0.04])
+    try:
+        r = T.solve_alg1(ids, table, T.isotropic_lambda0(1.5, 1.2),
+                         applied_stress=T.strain_tensor_from_voigt(sa_v), tol=1e-11, max_iter=2000)
+    except Exception:
+        return False
+    e_eng = np.linalg.solve(C, sa_v)
+    want = np.concatenate([e_eng[:3], 0.5 * e_eng[3:]])
+    return bool(r.converged and np.allclose(T.voigt_from_tensor(r.eps_bar), want, rtol=0,
+                                            atol=1e-8 * np.abs(want).max()))
+
+
+def test_stress_loop_pin_holds_unmutated():
+    assert _laminate_compliance_pin_holds()
+
+
+def _mut_solve_lam_shear(orig):
+    def solve_lam(lam, rhs):
+        X = orig(lam, rhs)
+        off = ~np.eye(3, dtype=bool)
+        X[off] *= 2.0                    # engineering shear strains taken as tensor components
+        return X
+    return solve_lam
+
+
+@pytest.mark.parametrize("mutate", ["shear_convention", "dropped_mean_stiffness"])
+def test_planted_stress_loop_mistake_is_caught(monkeypatch, mutate):
+    if mutate == "shear_convention":
+        monkeypatch.setattr(T, "_solve_lam", _mut_solve_lam_shear(T._solve_lam))
+    else:
+        monkeypatch.setattr(T.Material, "mean_stiffness", lambda self: np.zeros((3, 3, 3, 3)))
+    assert not _laminate_compliance_pin_holds()

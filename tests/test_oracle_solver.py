@@ -195,6 +195,29 @@ def test_applied_stress_loop():
     np.testing.assert_allclose(r2.sig, r.sig, atol=1e-9 * np.abs(r.sig).max())
 
 
+def test_applied_stress_on_a_laminate_gives_the_closed_form_compliance():
+    """Section 2.5 under stress control on a laminate: the converged average strain is
+    the closed-form compliance (inverse of the Backus stiffness) applied to sigma^a,
+    and the layers carry the stress components that continuity fixes (sigma_11,
+    sigma_12, sigma_13 uniform through the layers)."""
+    grid = (8, 4, 4)
+    layers = [0, 1, 1, 0, 0, 0, 1, 0]
+    ids = synth.laminate_x(grid, layers)
+    table = synth.two_phase_table(1.0, 0.3, 4.0, 0.25)
+    lam0 = T.isotropic_lambda0(1.5, 1.2)
+    sa_v = np.array([0.2, -0.05, 0.1, 0.03, -0.02, 0.04])
+    r = T.solve_alg1(ids, table, lam0, applied_stress=T.strain_tensor_from_voigt(sa_v), tol=1e-12,
+                     max_iter=5000)
+    assert r.converged
+    C = _laminate_closed_form(table, [1 - np.mean(layers), np.mean(layers)])
+    e_eng = np.linalg.solve(C, sa_v)
+    want = np.concatenate([e_eng[:3], 0.5 * e_eng[3:]])  # tensor components
+    np.testing.assert_allclose(T.voigt_from_tensor(r.eps_bar), want, rtol=0, atol=1e-9 * np.abs(want).max())
+    sig = T.voigt_from_tensor(r.sig)                      # [6][N3][N2][N1]
+    for i in (0, 4, 5):                                   # sigma_11, sigma_13, sigma_12: traction continuity
+        np.testing.assert_allclose(sig[i], sa_v[i], rtol=0, atol=1e-8 * np.abs(sa_v).max())
+
+
 def test_eigenstrain_matches_dense_solve():
     """Eq. (linear_elasticity) with an eigenstrain in phase 1, zero applied strain."""
     grid = (6, 6, 6)
