@@ -503,6 +503,8 @@ def run_ours(args):
         except Exception:  # noqa: BLE001 - pageable memory still gives an end-to-end number
             ids_host, host_mem = ids, "pageable"
         torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(args.steps):
@@ -514,10 +516,13 @@ def run_ours(args):
                 s.close()
                 del s
         torch.cuda.synchronize(dev)
-        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        e2e_ms, e_iters = combine_over_ranks(1e3 * (time.perf_counter() - t0), e_iters, dev, world)
+        e2e_s = e2e_ms / 1e3
         e2e = {"value": e_iters * N / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(len(tables) * (ids.nbytes + 2 * 36 * 8)),
-               "d2h_bytes_per_step": int(len(tables) * 6 * 6 * 8), "host_memory": host_mem}
+               "h2d_bytes_per_step": int(world * len(tables) * (ids.nbytes + 2 * 36 * 8)),
+               "d2h_bytes_per_step": int(world * len(tables) * 6 * 6 * 8), "host_memory": host_mem}
 
     # the same iteration through torch.fft (cuFFT) and torch elementwise kernels, outside the timed region
     lib_base = None
