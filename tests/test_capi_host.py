@@ -171,3 +171,40 @@ def test_create_rejects_null_coefficient_field(lib):
     st = lib.hs_create(ctypes.byref(ctx), g, ctypes.byref(m), None, ctypes.byref(o), ctypes.c_void_p(addr),
                        ctypes.c_size_t(256), None)
     assert st == hs.HS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value", [
+    ("check_every", 0), ("inner_max", 0), ("inner_ratio", 0.0), ("inner_ratio", 1.0), ("zchunk", -1),
+    ("ytile", 3), ("ytile", 16), ("xfuse", 2), ("col_tile", -1), ("col_tile", 12), ("col_threads", 48),
+    ("col_threads", 4096), ("use_graphs", 2),
+])
+def test_create_rejects_bad_options_before_any_device_work(lib, field, value):
+    from paper_2405_11168_gb300 import hs
+
+    ids = np.zeros((8, 8, 8), dtype=np.uint8)
+    table = np.eye(6).reshape(1, 36).copy()
+    m = hs.hs_material(hs.HS_IDS_U8, ctypes.c_void_p(ids.ctypes.data),
+                       table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1)
+    opt = hs.default_options(**{field: value})
+    ctx = ctypes.c_void_p()
+    grid = (ctypes.c_int * 3)(8, 8, 8)
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(m), None, ctypes.byref(opt), ctypes.c_void_p(1 << 20),
+                      1 << 30, None)
+    assert s == hs.HS_ERR_INVALID_ARG, (field, value, s)
+    assert ctx.value is None
+
+
+def test_create_rejects_non_finite_per_voxel_stiffness(lib):
+    from paper_2405_11168_gb300 import hs
+
+    coeffs = np.zeros((21, 8, 8, 8), dtype=np.float32)
+    coeffs[0] = 1.0
+    coeffs[2, 3, 4, 5] = np.inf
+    m = hs.hs_material(hs.HS_COEFFS_F32, None, None, 0, ctypes.c_void_p(coeffs.ctypes.data))
+    ctx = ctypes.c_void_p()
+    grid = (ctypes.c_int * 3)(8, 8, 8)
+    opt = hs.default_options()
+    s = lib.hs_create(ctypes.byref(ctx), grid, ctypes.byref(m), None, ctypes.byref(opt), ctypes.c_void_p(1 << 20),
+                      1 << 30, None)
+    assert s == hs.HS_ERR_INVALID_ARG
+    assert ctx.value is None
