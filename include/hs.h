@@ -244,12 +244,12 @@ hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
  * allocate at the moment it runs - real-time or embedded callers with a fixed memory budget,
  * callers whose device memory belongs entirely to another allocator (a caching pool), checks run
  * where an allocation could fail or stall - and who therefore cannot supply hs_create's
- * workspace.  It computes, in FP64, the nodal force F = dE/du of the tetrahedral-stencil energy
- * at the real-space corner displacement u (the residual of Algorithm 1 evaluated in real space),
- * the mean stress <sigma> and the L2 norm of F (Eq. L2-norm, real-space form), exactly as the
- * FP64 residual sweep of HS_FP32_REFINED does.
- *  grid       N1, N2, N3 as for hs_create.
- *  ids        device, uint16 phase ids [N3][N2][N1].
+ * workspace.  It computes, in FP64, the nodal force F = dE/du (the derivative of the
+ * tetrahedral-stencil elastic energy with respect to each corner displacement) at the real-space
+ * corner displacement u, the mean stress <sigma> and the root mean square of F, the same values
+ * the FP64 residual sweep of HS_FP32_REFINED computes.
+ *  grid       N1, N2, N3: the grids hs_create accepts (even, 4..512, prime factors 2, 3, 5, 7, 11).
+ *  ids        device, uint16 phase ids [N3][N2][N1]; every id must be < nphase.
  *  table      host, nphase x 36 Voigt stiffness (as hs_material.table); 1 <= nphase <= HS_NOALLOC_MAX_PHASES.
  *  E          host, macroscopic strain (tensor components, Voigt order).
  *  u          device, FP64 [3][N3][N2][N1]: u_k of the corner (l+1/2, m+1/2, n+1/2) at index (l, m, n).
@@ -261,7 +261,9 @@ hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
  * exits.  The first call on a device looks up that array's device address (with the device current), so
  * make that first call before any stream capture.  All calls share the array and each call resets what
  * must start from zero; calls that overlap on the GPU (other streams, other host threads) race on it.
- * Sizes beyond the limits above return HS_ERR_INVALID_ARG (phases) or HS_ERR_UNSUPPORTED_SIZE (grid). */
+ * Errors: HS_ERR_INVALID_ARG (null pointer, non-finite E or stiffness, nphase out of range, an id >= nphase,
+ * checked on the device before the residual runs), HS_ERR_UNSUPPORTED_SIZE (a grid hs_create refuses, more
+ * blocks than HS_NOALLOC_MAX_BLOCKS, or no row tile whose shared memory fits the device), HS_ERR_CUDA. */
 hs_status hs_residual_noalloc(const int grid[3], const unsigned short* ids, const double* table, int nphase,
                               const double E[6], const double* u, float* force, double sig_mean[6],
                               double* l2, void* stream);

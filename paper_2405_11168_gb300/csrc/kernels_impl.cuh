@@ -1,32 +1,37 @@
 // Definitions of the launchers in launch.h; included once per precision.
 #pragma once
+#include <map>
 #include <mutex>
 #include <type_traits>
-#include <unordered_map>
+#include <utility>
 
 #include "launch.h"
 
 namespace hs {
 
 // Raise a kernel's dynamic shared-memory limit when a launch needs more than
-// it has been given so far (process-wide, per kernel).  Launches recorded into
+// it has been given so far on the current device (the attribute is per device,
+// so the record is keyed by device ordinal and kernel).  Launches recorded into
 // a graph capture therefore never call the attribute API: the first,
 // uncaptured, chunk of a solve has already set it.
 inline std::mutex& smem_mu() {
   static std::mutex m;
   return m;
 }
-inline std::unordered_map<const void*, size_t>& smem_set() {
-  static std::unordered_map<const void*, size_t> m;
+inline std::map<std::pair<int, const void*>, size_t>& smem_set() {
+  static std::map<std::pair<int, const void*>, size_t> m;
   return m;
 }
 template <typename K> static cudaError_t set_smem(K kernel, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
-  const void* key = reinterpret_cast<const void*>(kernel);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const std::pair<int, const void*> key(dev, reinterpret_cast<const void*>(kernel));
   std::lock_guard<std::mutex> lock(smem_mu());
   size_t& have = smem_set()[key];
   if (smem <= have) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) have = smem;
   return e;
 }

@@ -30,7 +30,9 @@ constexpr size_t kTableBytes = (size_t)HS_NOALLOC_MAX_PHASES * 21 * sizeof(doubl
 constexpr size_t kPartialBytes = (size_t)HS_NOALLOC_MAX_BLOCKS * hs::NRED * sizeof(double);
 constexpr size_t kScratchBytes = kStatusBytes + kTableBytes + kPartialBytes;
 static_assert(kScratchBytes <= HS_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
-static_assert(sizeof(hs::DevStatus) + sizeof(double) <= kStatusBytes, "status record too large");
+// The last int of the status block receives the largest phase id of the call.
+constexpr size_t kMaxIdOffset = kStatusBytes - sizeof(int);
+static_assert(sizeof(hs::DevStatus) + sizeof(double) <= kMaxIdOffset, "status record too large");
 
 // Every device that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HS_NOALLOC_SCRATCH_BYTES];
@@ -74,10 +76,12 @@ bool isotropic(const double* C, double* lam, double* mu) {
   return true;
 }
 
+// The grids hs_create accepts: even, 4..512, prime factors 2, 3, 5, 7 and 11 (the
+// real-space pass itself needs no FFT plan, so every such length runs).
 bool supported(int n) {
   if (n < 4 || n > 512 || (n % 2) != 0) return false;
-  while (n % 2 == 0) n /= 2;
-  while (n % 3 == 0) n /= 3;
+  for (int f : {2, 3, 5, 7, 11})
+    while (n % f == 0) n /= f;
   return n == 1;
 }
 
@@ -93,13 +97,25 @@ extern "C" hs_status hs_residual_noalloc(const int grid[3], const unsigned short
   for (int i = 0; i < 6; ++i)
     if (!std::isfinite(E[i])) return HS_ERR_INVALID_ARG;
   const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
-  const int ty = (n2 % 4 == 0) ? 4 : 2;
+  const int nthr = ((n1 + 31) / 32) * 32;
+  // rows per block: 4 where N2 allows, halved while the plane ring does not fit
+  // in the device's opt-in shared memory (N1 = 512 needs 2)
+  int dev = 0, smem_optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return HS_ERR_CUDA;
+  int ty = (n2 % 4 == 0) ? 4 : 2;
+  size_t smem = hs::march_layout(n1, 0, nthr, ty, hs::MODE_FORCE, true, false, 8).total;
+  while (ty > 2 && smem > (size_t)smem_optin) {
+    ty /= 2;
+    smem = hs::march_layout(n1, 0, nthr, ty, hs::MODE_FORCE, true, false, 8).total;
+  }
+  if (smem > (size_t)smem_optin) return HS_ERR_UNSUPPORTED_SIZE;
   const int ytiles = n2 / ty;
   int nzc = std::max(1, std::min(n3, (608 + ytiles - 1) / ytiles));
   const int zc = (n3 + nzc - 1) / nzc;
   nzc = (n3 + zc - 1) / zc;
   if ((size_t)ytiles * nzc > (size_t)HS_NOALLOC_MAX_BLOCKS) return HS_ERR_UNSUPPORTED_SIZE;
-  const int nthr = ((n1 + 31) / 32) * 32;
 
   // phase table in the kernel's layout
   bool iso = true;
@@ -131,19 +147,34 @@ extern "C" hs_status hs_residual_noalloc(const int grid[3], const unsigned short
   double* hist = reinterpret_cast<double*>(base + sizeof(hs::DevStatus));
   double* mat = reinterpret_cast<double*>(base + kStatusBytes);
   double* partials = reinterpret_cast<double*>(base + kStatusBytes + kTableBytes);
+
+  int* maxid = reinterpret_cast<int*>(base + kMaxIdOffset);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nvox = (size_t)n1 * n2 * n3;
 
   // The array keeps the previous call's contents: reset the status record
-  // (block-arrival counter, flags) and load this call's phase table.
+  // (block-arrival counter, flags) and the max-id slot, and load this call's
+  // phase table.
+  unsigned char head[kStatusBytes];
+  memset(head, 0, sizeof(head));
   hs::DevStatus h;
   memset(&h, 0, sizeof(h));
   h.max_iter = 1 << 30;
   h.hist_cap = 1;
-  h.nvox = (double)n1 * n2 * n3;
-  e = cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+  h.nvox = (double)nvox;
+  memcpy(head, &h, sizeof(h));
+  e = cudaMemcpyAsync(base, head, kStatusBytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(mat, packed, (size_t)nphase * (iso ? 2 : 21) * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return HS_ERR_CUDA;
+  // Every id must index the table: the stress kernel reads the table at the
+  // id without a bound, so an id >= nphase is refused before it runs.
+  int hmax = 0;
+  e = hs::launch_max_id(ids, nvox, maxid, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hmax, maxid, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return HS_ERR_CUDA;
+  if (hmax >= nphase) return HS_ERR_INVALID_ARG;
 
   hs::MarchArgs<double> a;
   memset(&a, 0, sizeof(a));
@@ -162,7 +193,6 @@ extern "C" hs_status hs_residual_noalloc(const int grid[3], const unsigned short
   a.fout = force;
   a.fout_f32 = 1;
   a.skip_if_done = 0;
-  const size_t smem = hs::march_layout(n1, 0, nthr, ty, hs::MODE_FORCE, true, false, 8).total;
   e = hs::launch_march<double>(a, iso, ty, hs::MODE_FORCE, true, dim3(ytiles, nzc), nthr, smem, s);
   if (e != cudaSuccess) return HS_ERR_CUDA;
   e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);

@@ -359,3 +359,54 @@ def test_refined_budget_end_writes_fields_in_the_last_sweep(hs):
     assert rel(eps, e_ref) < 2e-5
     assert rel(sig, s_ref) < 2e-5
     s.close()
+
+
+def test_fp32_anisotropic_polycrystal_iterate_by_iterate(hs):
+    """The FP32 anisotropic constitutive step (21 coefficients per grain) against the oracle:
+    a 48^3 periodic Voronoi polycrystal of 24 grains (cubic C11 = 168.4, C12 = 121.4,
+    C44 = 75.4 GPa rotated by uniform random rotations, the 512^3 polycrystal's material at a
+    size the oracle runs), shear E12 = 1e-3, isotropic reference medium with
+    K0 = (C11 + 2 C12)/3 and mu0 = (C44 + (C11 - C12)/2)/2 given to both sides: the same
+    error history (FP32 rounding, 2e-5) and fields within 1e-5 after 6 evaluations."""
+    grid = (48, 48, 48)
+    ids, _ = synth.voronoi_grains(grid, 24, seed=2)
+    table = synth.polycrystal_table(168.4, 121.4, 75.4, synth.random_rotations(24, seed=3))
+    K0 = (168.4 + 2 * 121.4) / 3
+    mu0 = 0.5 * (75.4 + 0.5 * (168.4 - 121.4))
+    lam0 = K0 - 2 * mu0 / 3
+    C0 = np.zeros((6, 6))
+    C0[:3, :3] = lam0
+    C0[[0, 1, 2], [0, 1, 2]] = lam0 + 2 * mu0
+    C0[[3, 4, 5], [3, 4, 5]] = mu0
+    E12 = np.array([0, 0, 0, 0, 0, 1e-3])
+    s = hs.Solver(ids, table, C0=C0, precision=hs.HS_FP32)
+    out = s.solve(E12, tol=0.0, max_iter=6)
+    assert out["status"] == hs.HS_NOT_CONVERGED and out["iters"] == 6
+    ref = T.solve_alg1(ids, table, T.stiffness_tensor(C0), T.strain_tensor_from_voigt(E12), tol=0.0, max_iter=6)
+    np.testing.assert_allclose(s.err_history(), ref.errs, rtol=2e-5)
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-5
+    assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-5
+    se = T.voigt_from_tensor(ref.sig_mean)
+    np.testing.assert_allclose(out["sig_eff"], se, rtol=0, atol=1e-5 * np.abs(se).max())
+    s.close()
+
+
+def test_refined_path_rigid_surrogate(hs):
+    """The rigid surrogate E_i/E_m = 1e6 (f = 0.2 sphere at 24^3) under FP32 iterations with FP64
+    residual sweeps.  The FP64 oracle's error floor on this cell is about 1.5e-10 (it reaches
+    1e-9 after about 460 evaluations), so the refined solve is asked for 1e-8 and compared
+    with the oracle stopped at 1e-9."""
+    ids, table = sphere_case((24, 24, 24), 1e6)
+    s = hs.Solver(ids, table, precision=hs.HS_FP32_REFINED)
+    out = s.solve(E11, tol=1e-8, max_iter=5000)
+    assert out["status"] == hs.HS_OK and out["err"] < 1e-8
+    ref = T.solve_alg1(ids, table, T.c0_alpha_rule(table), T.strain_tensor_from_voigt(E11), tol=1e-9,
+                       max_iter=1000)
+    assert ref.converged
+    e_ref, s_ref = voigt_fields(ref)
+    assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-6
+    assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-6
+    se = T.voigt_from_tensor(ref.sig_mean)
+    np.testing.assert_allclose(out["sig_eff"], se, rtol=0, atol=1e-7 * np.abs(se).max())
+    s.close()

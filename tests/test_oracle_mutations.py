@@ -166,3 +166,40 @@ def test_planted_stress_loop_mistake_is_caught(monkeypatch, mutate):
     else:
         monkeypatch.setattr(T.Material, "mean_stiffness", lambda self: np.zeros((3, 3, 3, 3)))
     assert not _laminate_compliance_pin_holds()
+
+
+# ---- the reference-medium rule (Section 3.4) ----------------------------------------------
+def _mut_alpha_swapped(orig):
+    def c0_alpha_rule(table):
+        table = np.asarray(table, dtype=np.float64)
+        lam_m, mu_m = table[0, 0, 1], table[0, 3, 3]
+        lam_i, mu_i = table[1, 0, 1], table[1, 3, 3]
+        k_m, k_i = lam_m + 2 * mu_m / 3, lam_i + 2 * mu_i / 3
+        alpha = 0.45 if k_i < k_m else 0.55            # the two weights exchanged
+        k0 = alpha * k_m + (1 - alpha) * k_i
+        nu0 = lam_m / (2 * (lam_m + mu_m))
+        mu0 = 3 * k0 * (1 - 2 * nu0) / (2 * (1 + nu0))
+        return T.isotropic_lambda0(k0 - 2 * mu0 / 3, mu0)
+    return c0_alpha_rule
+
+
+def _mut_nu_from_inclusion(orig):
+    def c0_alpha_rule(table):
+        table = np.asarray(table, dtype=np.float64)
+        lam0 = orig(table)
+        # Poisson ratio taken from phase 1 instead of the matrix: same k0, other split
+        lam_i, mu_i = table[1, 0, 1], table[1, 3, 3]
+        nu_i = lam_i / (2 * (lam_i + mu_i)) if (lam_i + mu_i) > 0 else 0.0
+        k0 = (lam0[0, 0, 0, 0] + 2 * lam0[0, 0, 1, 1]) / 3
+        mu0 = 3 * k0 * (1 - 2 * nu_i) / (2 * (1 + nu_i))
+        return T.isotropic_lambda0(k0 - 2 * mu0 / 3, mu0)
+    return c0_alpha_rule
+
+
+@pytest.mark.parametrize("factory", [_mut_alpha_swapped, _mut_nu_from_inclusion])
+def test_planted_reference_medium_mistake_is_caught(monkeypatch, factory):
+    from tests.test_oracle_c0_rule import alpha_rule_matches_golden
+
+    assert alpha_rule_matches_golden()
+    monkeypatch.setattr(T, "c0_alpha_rule", factory(T.c0_alpha_rule))
+    assert not alpha_rule_matches_golden()
