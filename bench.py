@@ -12,6 +12,16 @@ FP64 residual sweeps, fields written.
 Metric: voxel-iterations/s = sum over solves of N x (residual evaluations),
 divided by the device time of the step (CUDA events, max over ranks).
 
+Beside the metric the line carries, each from its own leg outside the timed
+region: the iterations and final errors per contrast of the timed solves and the
+oracle's own error at one solve's final state (``err_vs_oracle``); a timing of
+one solve that runs the FP32 correction solves (``correction_solves``); 18
+solves at 64^3 served to equilibrium error <= 1e-6 in plain FP64 and in FP32 +
+FP64 refinement (``converged``: solves/s, p50/p99, the oracle's error at the
+served states); 64 RVEs of sizes 32^3..128^3 with their 6 load cases in one
+batch against the same solves one by one (``batched``); and a Poisson-arrival
+request stream through the serving runtime (``serving``).
+
 ``--impl reference`` times the CPU FP64 oracle instead (one Algorithm-1
 iteration of the same 256^3 problem per step, on the host cores).
 """
@@ -45,9 +55,9 @@ TOL = 1e-6
 # whichever comes first, and reports how many reached TOL.
 BUDGET = 64
 # DRAM bytes (read + write) per launch of the dominant kernel at the 256^3
-# workload, from one ncu --set full capture of the current kernel (summarised
-# with its command in profiles/iteration_kernels_256_fp32.md); set to None
-# whenever that kernel changes until it is captured again.
+# workload, from one ncu capture of the current kernel (its summary, with the
+# command, is kept under profiles/); set to None whenever that kernel changes
+# until it is captured again.
 NCU_TRAFFIC = {"xpass": 413.2e6}
 METRIC = "voxel-iterations/s"
 UNIT = "voxel-iter/s"
@@ -354,6 +364,211 @@ def combine_over_ranks(ms, iters, device, world):
     return float(t.item()), float(it.item())
 
 
+def oracle_err_at(u_real, ids, table, E6):
+    """The oracle's equilibrium error (Eqs. L2-norm, tolerance) and <sigma> at a real-space
+    corner displacement (corner (l+1/2, m+1/2, n+1/2) at index (l, m, n)): Algorithm 1 steps
+    1-4 evaluated once at that state, in FP64 on the host."""
+    from oracle import tetra as T
+
+    n3, n2, n1 = ids.shape
+    grid = (n1, n2, n3)
+    q1, q2, q3 = T.q_vectors(grid)
+    u_q = T.ft(np.asarray(u_real, dtype=np.float64)) * np.exp(-0.5j * (q1 + q2 + q3))[None]
+    _, _, _, _, _, L2, sm = T.evaluate(u_q, T.D_of_q(grid), T.Material(ids, table), T.strain_tensor_from_voigt(E6),
+                                       grid)
+    return float(L2 / np.sqrt(np.sum(sm ** 2))), T.voigt_from_tensor(sm)
+
+
+def state_check(s, ids, table, E6, gpu_err, gpu_sig):
+    """The oracle's error and <sigma> at a solver's final displacement against what the GPU reported."""
+    err, sm = oracle_err_at(s.get_displacement().cpu().numpy(), ids, table, E6)
+    return {"gpu_err": gpu_err, "oracle_err_at_gpu_state": err,
+            "err_rel_diff": abs(err - gpu_err) / max(err, 1e-300),
+            "sig_eff_rel_diff": float(np.max(np.abs(np.asarray(gpu_sig) - sm)) / np.max(np.abs(sm)))}
+
+
+def per_contrast(log):
+    """Iterations and final errors of logged solves, by contrast."""
+    out = {}
+    for c in sorted({x["contrast"] for x in log}, key=lambda v: -v):
+        xs = [x for x in log if x["contrast"] == c]
+        out[f"{c:g}"] = {"solves": len(xs), "converged": sum(x["status"] == 0 for x in xs),
+                         "evaluations": sorted({x["iters"] for x in xs}),
+                         "final_err_min": min(x["err"] for x in xs), "final_err_max": max(x["err"] for x in xs)}
+    return out
+
+
+def correction_leg(hs, ids_dev, table, dev, stream):
+    """One 256^3 solve whose budget runs FP32 correction solves: the first FP32 solve and every
+    correction solve get at most 40 evaluations, 200 in all, every launch timed."""
+    s = hs.Solver(ids_dev, table, precision=hs.HS_FP32_REFINED, device=dev, stream=stream, inner_max=40)
+    E = unit_loads()[0]
+    s.solve(E, tol=TOL, max_iter=200, fields=False)
+    s.profile_read()
+    s.profile(1)
+    out = s.solve(E, tol=TOL, max_iter=200, fields=False)
+    prof = s.profile_read()
+    s.profile(False)
+    hist = s.err_history()
+    s.close()
+    kern = {k: {"ms_per_launch": round(t / n, 4), "launches": n,
+                "gbs": (round(algorithmic_bytes(k, GRID) / (t / n / 1e3) / 1e9, 1) if algorithmic_bytes(k, GRID) else None)}
+            for k, (t, n) in prof.items() if n}
+    return {"what": f"{GRID[0]}^3 contrast {CONTRASTS[0]:g} E11, inner_max 40, budget 200 evaluations, every launch "
+                    "timed with CUDA events", "evaluations": out["iters"], "status": out["status"],
+            "final_err": out["err"], "fp64_sweep_errs": [float(x) for x in hist[40:]][-8:], "kernels": kern}
+
+
+CONV_GRID = (64, 64, 64)
+CONV_CONTRASTS = [1e3, 1e-3, 0.0]
+
+
+def converged_leg(hs, dev):
+    """18 solves (64^3 random spheres R = 8, f = 0.30, seed 1; contrasts 1e3, 1e-3 and voids, 6 unit
+    loads each) served to err <= 1e-6 through the resident serving runtime, in plain FP64 and in
+    FP32 + FP64 refinement; the first pass creates the resident contexts, the second is timed.
+    The oracle's own error at each contrast's E11 state is reported beside the GPU's.  The rigid
+    surrogate 1e6 is run alone with a 3000-evaluation budget in both precisions."""
+    from paper_2405_11168_gb300 import serve
+
+    ids, _ = synth.random_spheres(CONV_GRID, RADIUS, FRACTION, SEED)
+    N = int(np.prod(CONV_GRID))
+    out = {"workload": f"{CONV_GRID[0]}^3 random spheres R=8 f=0.30 seed 1, contrasts {CONV_CONTRASTS}, "
+                       "6 unit loads each (18 solves), tol 1e-6, 3 serving slots, resident contexts"}
+    for name, prec in (("fp64", hs.HS_FP64), ("fp32_refined", hs.HS_FP32_REFINED)):
+        tables = [synth.two_phase_table(1.0, NU, c, NU) for c in CONV_CONTRASTS]
+        srv = serve.Server(budget_bytes=40 << 30, slots=3, device=dev)
+        try:
+            def reqs():
+                return [serve.Request(ids=ids, table=t, loads=unit_loads(), precision=prec, tol=TOL, max_iter=20000,
+                                      tag=c) for t, c in zip(tables, CONV_CONTRASTS)]
+            serve.run_stream(srv, reqs(), 0.0)
+            res, wall = serve.run_stream(srv, reqs(), 0.0)
+        finally:
+            srv.close()
+        solves = sum(len(r.iters) for r in res)
+        evals = sum(sum(r.iters) for r in res)
+        row = {"solves_per_s": solves / wall, "solves": solves, "wall_s": wall,
+               "converged": sum(int(st == hs.HS_OK) for r in res for st in r.status),
+               "voxel_iter_per_s": evals * N / wall, "evaluations": {f"{r.tag:g}": r.iters for r in res},
+               "final_err_max": max(max(r.errs) for r in res), **serve.latency_stats(res),
+               "latency_is": "per request (6 solves), all 3 requests submitted at once", "err_vs_oracle": {}}
+        for t, c in zip(tables, CONV_CONTRASTS):
+            s = hs.Solver(ids, t, precision=prec, device=dev)
+            o = s.solve(unit_loads()[0], tol=TOL, max_iter=20000, fields=False)
+            row["err_vs_oracle"][f"{c:g}"] = state_check(s, ids, t, unit_loads()[0], o["err"], o["sig_eff"])
+            s.close()
+        rig = hs.Solver(ids, synth.two_phase_table(1.0, NU, 1e6, NU), precision=prec, device=dev)
+        o = rig.solve(unit_loads()[0], tol=TOL, max_iter=3000, fields=False)
+        rig.close()
+        row["rigid_1e6_E11"] = {"status": o["status"], "evaluations": o["iters"], "final_err": o["err"]}
+        out[name] = row
+    out["refined_over_fp64_solves_per_s"] = out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
+BATCH_SIZES = (32, 48, 64, 96, 128)
+
+
+def batch_rves(n_rve=64, seed=4):
+    """64 RVEs: sizes uniform over 32^3..128^3; half random spheres (R = 8, f = 0.30, contrast
+    log-uniform in 1e-3..1e3), half 50-grain cubic Voronoi polycrystals (C11 = 168.4,
+    C12 = 121.4, C44 = 75.4 rotated per grain)."""
+    rng = np.random.default_rng(seed)
+    rves = []
+    for _ in range(n_rve):
+        n = int(rng.choice(BATCH_SIZES))
+        if rng.random() < 0.5:
+            ids, _ = synth.random_spheres((n, n, n), RADIUS, FRACTION, int(rng.integers(1 << 30)))
+            table = synth.two_phase_table(1.0, NU, float(10.0 ** rng.uniform(-3, 3)), NU)
+        else:
+            ids, _ = synth.voronoi_grains((n, n, n), 50, seed=int(rng.integers(1 << 30)))
+            ids = ids.astype(np.uint8)
+            table = synth.polycrystal_table(168.4, 121.4, 75.4, synth.random_rotations(50, seed=int(rng.integers(1 << 30))))
+        rves.append((ids, table))
+    return rves
+
+
+def batched_leg(hs, dev, budget=200):
+    """The 64 RVEs x 6 load cases (384 items) in one batch against the same 384 solves one by one
+    (one resident solver per RVE), FP32 + FP64 refinement, tol 1e-6, the same evaluation budget per
+    solve; the iterates are identical either way, so the two voxel-iteration rates compare the same
+    work."""
+    rves = batch_rves()
+    item_rve = [r for r in range(len(rves)) for _ in range(6)]
+    E = np.array([e for _ in rves for e in unit_loads()])
+    Ns = np.array([rves[r][0].size for r in item_rve], dtype=np.float64)
+    stream = torch_stream(dev)
+    b = hs.Batch(rves, item_rve, precision=hs.HS_FP32_REFINED, device=dev, stream=stream, autotune=True)
+    nclass, _ = b.classes()
+    b.solve(E, tol=TOL, max_iter=budget)
+    b.launches()
+    t0 = cuda_time(dev, stream)
+    ob = b.solve(E, tol=TOL, max_iter=budget)
+    tb = cuda_time(dev, stream) - t0
+    launches_b = b.launches()
+    b.close()
+    del b
+    solvers = [hs.Solver(ids, t, precision=hs.HS_FP32_REFINED, device=dev, stream=stream) for ids, t in rves]
+    for s in solvers:
+        s.solve(unit_loads()[0], tol=TOL, max_iter=budget, fields=False)
+    t0 = cuda_time(dev, stream)
+    it1 = []
+    for i, r in enumerate(item_rve):
+        it1.append(solvers[r].solve(E[i], tol=TOL, max_iter=budget, fields=False)["iters"])
+    t1 = cuda_time(dev, stream) - t0
+    for s in solvers:
+        s.close()
+    vb = float(np.sum(ob["iters"] * Ns)) / tb
+    v1 = float(np.sum(np.array(it1) * Ns)) / t1
+    return {"workload": f"64 RVEs, sizes from {list(BATCH_SIZES)}^3, random spheres (contrast log-uniform 1e-3..1e3) "
+                        "or 50-grain cubic Voronoi, 6 unit loads each (384 items), FP32 + FP64 refinement, "
+                        f"tol 1e-6, budget {budget} evaluations per item",
+            "size_classes": nclass, "voxel_iter_per_s_batched": vb, "voxel_iter_per_s_one_by_one": v1,
+            "speedup": vb / v1, "s_batched": tb, "s_one_by_one": t1,
+            "items_converged": int(np.sum(ob["item_status"] == 0)), "evaluations_total": int(np.sum(ob["iters"])),
+            "same_evaluations_one_by_one": bool(np.array_equal(ob["iters"], np.array(it1))),
+            "gpu_launches_batched": launches_b}
+
+
+def serving_leg(hs, dev, n=40, rate=2.0, sizes=(64, 96, 128)):
+    """A Poisson-arrival stream through the serving runtime: the request mix of the serving
+    configuration (random spheres with contrast log-uniform in 1e-3..1e3, 5 % voids, 5 % rigid
+    surrogate, or 50-grain Voronoi; 1-6 load cases) at sizes up to 128^3, FP32 + FP64 refinement,
+    err <= 1e-6 or 3000 evaluations, a 150 GB budget."""
+    from paper_2405_11168_gb300 import serve
+
+    reqs = serve.synthetic_requests(n, list(sizes), 5, hs.HS_FP32_REFINED, TOL, 3000)
+    srv = serve.Server(int(150 * 2 ** 30), slots=8, device=dev)
+    try:
+        res, wall = serve.run_stream(srv, reqs, rate, seed=5)
+    finally:
+        srv.close()
+    solves = sum(len(r.iters) for r in res)
+    return {"workload": f"{n} requests, sizes {list(sizes)}^3, Poisson arrivals at {rate} /s, 8 slots, 150 GB budget, "
+                        "FP32 + FP64 refinement, tol 1e-6, budget 3000 evaluations per solve",
+            "solves_per_s": solves / wall, "solves": solves, "wall_s": wall,
+            "converged": sum(int(st == hs.HS_OK) for r in res for st in r.status), **serve.latency_stats(res),
+            "contexts_created": srv.created, "contexts_released": srv.released, "max_running": srv.max_running,
+            "max_resident_gb": srv.max_used / 2 ** 30}
+
+
+def torch_stream(dev):
+    import torch
+
+    return torch.cuda.Stream(dev)
+
+
+def cuda_time(dev, stream):
+    """Host clock after the stream drained (the legs above are timed end to end on the host)."""
+    stream.synchronize()
+    import torch
+
+    torch.cuda.synchronize(dev)
+    return time.perf_counter()
+
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -410,7 +625,7 @@ def run_ours(args):
 
     conv_log = []
 
-    def solve_one(s, E):
+    def solve_one(s, E, contrast=None):
         E = np.ascontiguousarray(E)
         sig_eff = np.zeros(6)
         it = ctypes.c_int()
@@ -420,16 +635,16 @@ def run_ours(args):
                             ctypes.byref(err))
         if st < 0:
             raise RuntimeError(f"solve failed: status {st}, err {err.value}")
-        conv_log.append((st == hs.HS_OK, err.value))
+        conv_log.append({"contrast": contrast, "status": int(st), "iters": int(it.value), "err": float(err.value)})
         return it.value, sig_eff
 
     def step():
         iters = 0
         C = []
-        for s in solvers:
+        for s, c in zip(solvers, CONTRASTS):
             Ceff = np.zeros((6, 6))
             for J, E in enumerate(loads):
-                k, se = solve_one(s, E)
+                k, se = solve_one(s, E, c)
                 iters += k
                 Ceff[:, J] = se
             C.append(Ceff)
@@ -511,7 +726,7 @@ def run_ours(args):
             for t in tables:
                 s = hs.Solver(ids_host, t, precision=prec, device=dev, stream=stream)
                 for E in loads:
-                    k, se = solve_one(s, E)
+                    k, se = solve_one(s, E, None)
                     e_iters += k
                 s.close()
                 del s
@@ -551,6 +766,29 @@ def run_ours(args):
                "sample": "one Algorithm-1 iteration (evaluation + update) of the 256^3 contrast-1e3 E11 solve, "
                          f"{t:.1f} s"}
 
+    legs = {}
+    if rank == 0 and world == 1:
+        # the oracle's own error at one timed solve's final state (contrast CONTRASTS[0], E11)
+        if not args.skip_cpu:
+            s0 = hs.Solver(ids_dev, tables[0], precision=prec, device=dev, stream=stream)
+            o = s0.solve(loads[0], tol=TOL, max_iter=BUDGET, fields=False)
+            legs["err_vs_oracle"] = dict(state_check(s0, ids, tables[0], loads[0], o["err"], o["sig_eff"]),
+                                         what=f"the {GRID[0]}^3 contrast-{CONTRASTS[0]:g} E11 solve of the step "
+                                              f"({BUDGET} evaluations): the oracle's FP64 evaluation (Algorithm 1 "
+                                              "steps 1-4) at the GPU's final displacement")
+            s0.close()
+        for name, fn in (("correction_solves", lambda: correction_leg(hs, ids_dev, tables[0], dev, stream)),
+                         ("converged", lambda: converged_leg(hs, dev)),
+                         ("batched", lambda: batched_leg(hs, dev)),
+                         ("serving", lambda: serving_leg(hs, dev))):
+            if name in args.skip_legs:
+                continue
+            try:
+                torch.cuda.empty_cache()
+                legs[name] = fn()
+            except Exception as e:  # noqa: BLE001 - a leg that fails is reported, the line still prints
+                legs[name] = {"error": f"{type(e).__name__}: {e}"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -559,8 +797,9 @@ def run_ours(args):
             "config": dict(workload_config("FP32 iterations + FP64 residual sweeps"),
                            parallelism=f"replicas x{world}"),
             "iterations_per_step": total_iters / args.steps,
-            "solves_converged": f"{sum(c for c, _ in timed_conv)}/{len(timed_conv)}",
-            "final_err_max": max(e for _, e in timed_conv),
+            "solves_converged": f"{sum(x['status'] == 0 for x in timed_conv)}/{len(timed_conv)}",
+            "final_err_max": max(x["err"] for x in timed_conv),
+            "per_contrast": per_contrast(timed_conv),
             "roofline": roof, "kernels": breakdown,
             "kernel_timing": f"CUDA events on the solver stream: one iteration chunk in {PROFILE_EVERY} (plain "
                              "launches) and every launch outside the chunks; the other chunks replay CUDA graphs",
@@ -570,6 +809,7 @@ def run_ours(args):
                                    "(30 x 4 B + 1 B) / measured HBM peak"},
             "torch_fft_baseline": lib_base,
             "gpu_launches": launches, "clocks": clocks,
+            **legs,
         }
         print(json.dumps(line), flush=True)
     for s in solvers:
@@ -609,7 +849,10 @@ def main():
     ap.add_argument("--skip-torch", action="store_true", help="skip the torch.fft comparison pipeline")
     ap.add_argument("--grid", type=int, default=256, help="cubic grid size (profiling runs use smaller cases)")
     ap.add_argument("--ncontrast", type=int, default=4, help="use the first k contrasts (profiling runs)")
+    ap.add_argument("--skip-legs", default="", help="comma-separated legs to skip: correction_solves, converged, "
+                                                    "batched, serving")
     args = ap.parse_args()
+    args.skip_legs = [x for x in args.skip_legs.split(",") if x]
     global GRID, CONTRASTS
     GRID = (args.grid,) * 3
     CONTRASTS = CONTRASTS[: max(1, min(4, args.ncontrast))]

@@ -142,6 +142,31 @@ hs_status hs_workspace_size(const int grid[3], int nphase, const hs_options* opt
 hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m, const double C0[36],
                     const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream);
 
+/* hs_create with the workspace layout sized for layout_nphase phases (nphase <= layout_nphase <=
+ * HS_MAX_PHASES; size the workspace with hs_workspace_size(grid, layout_nphase, opt)), so that
+ * hs_set_material can later bind any material of up to layout_nphase phases.  Otherwise as
+ * hs_create. */
+hs_status hs_create_sized(hs_ctx** out, const int grid[3], const hs_material* m, const double C0[36],
+                          const hs_options* opt, int layout_nphase, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Bind a context to another microstructure of the same grid, keeping its workspace, launch
+ * configuration and captured iteration graphs resident (a serving slot reused for a new
+ * request).  The phase ids and table are copied in (m as for hs_create; at most the phase count
+ * the layout was sized for) and the reference medium is chosen again (C0, or the policy when
+ * NULL).  Captured graphs stay valid when the reference medium is isotropic and the phases stay
+ * isotropic (or stay anisotropic); otherwise the next solve captures them again.  Removes any
+ * eigenstrain and warm-start state.
+ * Errors: as hs_create.  After an error the context holds no valid material and refuses to
+ * solve until a later hs_set_material succeeds. */
+hs_status hs_set_material(hs_ctx* c, const hs_material* m, const double C0[36]);
+
+/* Real-space corner displacement of the last solve's final evaluation, FP64 [3][N3][N2][N1]
+ * (u_k of the corner (l+1/2, m+1/2, n+1/2) at index (l, m, n)), device pointer: the FP64
+ * displacement of HS_FP32_REFINED, or the inverse transform of the state that the last
+ * evaluation of HS_FP64 / HS_FP32 read (FP32 values widened). */
+hs_status hs_get_displacement(hs_ctx* c, double* u);
+
 /* Solve for one applied macroscopic strain (Algorithm 1 under strain control).
  *  E          host, 6 tensor components in Voigt order; all zero only with an eigenstrain set.
  *  tol        stop at the first evaluation with err < tol (tol = 0: run max_iter evaluations).
@@ -233,6 +258,70 @@ hs_status hs_profile_enable(hs_ctx* c, int on);
  * class were timed, ms is their total scaled by (launches / timed launches), so ms / launches is
  * the mean time of the timed launches. */
 hs_status hs_profile_read(hs_ctx* c, double ms[10], long long launches[10]);
+
+/* ---- Batched solves: many RVEs and their load cases in shared launches ----------------------
+ * An item is one microstructure (RVE) under one macroscopic strain; the 6 unit strains of an RVE
+ * give its effective 6x6 stiffness (Eq. final_fields, <sigma> per load case).  Items whose RVEs
+ * share a grid and phase isotropy form a size class.  Every item owns a full single-solve
+ * workspace (hs_workspace_size of its RVE's grid, with the class's largest phase count); the items
+ * of a class lie one stride apart in the batch workspace, and every kernel of a class runs as ONE
+ * launch over all its items.  A chunk of check_every iterations of every class is captured as one
+ * CUDA graph (the classes on streams forked from the batch stream, so they overlap) and replayed
+ * until every item has stopped.  Each item has its own status and stopping test, its own reference
+ * medium (the C0 policy of hs_create) and its own error history, and the same iterates as a
+ * single hs_solve of that item (reductions run in the same order). */
+typedef struct hs_batch hs_batch;
+
+/* Workspace bytes of a batch.
+ *  nrve       number of RVEs; grids: host nrve x 3 (N1, N2, N3, as hs_create); nphase: host nrve.
+ *  nitem      number of items; item_rve: host nitem RVE indices in 0..nrve-1 (any order; an RVE
+ *             may appear several times).
+ *  opt        shared options (precision; xfuse must be 0).
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED_SIZE (a grid hs_create refuses). */
+hs_status hs_batch_workspace_size(int nrve, const int* grids, const int* nphase, int nitem, const int* item_rve,
+                                  const hs_options* opt, size_t* bytes);
+
+/* Create a batch.
+ *  mats       host nrve materials, ids kinds only (HS_IDS_U8 / HS_IDS_U16; compress a per-voxel
+ *             field with hs_compress_coefficients first); read during this call.
+ *  autotune   1: each class takes its launch shapes from hs_autotune's plan cache, tuning on the
+ *             class's first workspace when the cache has no plan for that grid; 0: opt as given.
+ *  workspace  device memory of at least hs_batch_workspace_size bytes, 256-byte aligned, owned by
+ *             the caller, in use until hs_batch_destroy.   stream: cudaStream_t (NULL = legacy
+ *             default stream, which cannot be captured: plain launches then).
+ * Errors: as hs_create; HS_ERR_OOM for a small workspace. */
+hs_status hs_batch_create(hs_batch** out, int nrve, const int* grids, const hs_material* mats, int nitem,
+                          const int* item_rve, const hs_options* opt, int autotune, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Solve every item (Algorithm 1 under strain control, in the batch's precision).
+ *  E          host nitem x 6: item i's macroscopic strain (tensor components, Voigt order), not 0.
+ *  tol, max_iter  as hs_solve, for every item.
+ *  sig_eff    host nitem x 6: <sigma> of the last evaluation of each item.
+ *  iters, final_err, status  host nitem: evaluations used, err of the last evaluation, and the
+ *             hs_status each item would have from hs_solve (HS_OK, HS_NOT_CONVERGED, HS_DIVERGED).
+ * HS_FP32_REFINED runs every item's stages in step: its plain FP32 first solve, then FP64
+ * residual sweeps (which take every stop decision) alternating with FP32 correction solves; an
+ * item that stops retires and every kernel skips it.  No fields are written.
+ * Returns HS_OK when every item converged, HS_NOT_CONVERGED otherwise, or an error. */
+hs_status hs_batch_solve(hs_batch* b, const double* E, double tol, int max_iter, double* sig_eff, int* iters,
+                         double* final_err, int* status);
+
+/* Error history of item `item` after the last hs_batch_solve: every evaluation (HS_FP64, HS_FP32),
+ * or one value per FP64 residual sweep (HS_FP32_REFINED).  Writes min(n, available) values. */
+hs_status hs_batch_err_history(const hs_batch* b, int item, double* out, int n, int* n_written);
+
+/* Kernel launches of the batch since the last call (replayed graph nodes counted per replay). */
+hs_status hs_batch_launches(hs_batch* b, long long* launches);
+
+/* Number of size classes, and (if class_of_item is not NULL) the class of every item. */
+hs_status hs_batch_classes(const hs_batch* b, int* nclass, int* class_of_item);
+
+/* Text of the last error of this batch (or of the last failed create). */
+const char* hs_batch_last_error(const hs_batch* b);
+
+/* Release the batch (the workspace stays the caller's). */
+void hs_batch_destroy(hs_batch* b);
 
 /* Limits of hs_residual_noalloc's fixed scratch array. */
 #define HS_NOALLOC_SCRATCH_BYTES (512 * 1024) /* bytes held on every device that loads the library */

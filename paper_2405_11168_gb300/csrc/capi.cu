@@ -185,7 +185,7 @@ bool cholesky_pd(const double* A) {
 }
 
 struct Layout {
-  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, u64, rsrc, total;
+  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, c0, u64, rsrc, total;
 };
 
 }  // namespace
@@ -202,6 +202,14 @@ struct hs_ctx {
   std::vector<double> table;
   double C0[36];
   double G6[36];
+  bool c0_iso = false;      // the reference medium is isotropic: Omega^-1 = c0_a M + c0_b tr(M) I
+  double c0_a = 0, c0_b = 0;
+  // batched launches (hs_batch): the kernels of this context run over batch_n items whose
+  // workspaces follow one another batch_stride bytes apart (1 and 0 for a single solve)
+  int batch_n = 1;
+  size_t batch_stride = 0;
+  int layout_np = 1;        // phase count the workspace layout was sized for (>= nphase)
+  bool unbound = false;     // a failed hs_set_material left the workspace without a valid material
   char* ws;
   size_t ws_bytes;
   Layout lay;
@@ -267,6 +275,12 @@ hs_status fail(hs_ctx* c, hs_status s, const std::string& msg) {
 
 hs_status cuda_fail(hs_ctx* c, cudaError_t e, const char* where) {
   return fail(c, HS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// A launch grid extended over the items of a batched context.
+dim3 zg(const hs_ctx* c, dim3 g) {
+  g.z = (unsigned)c->batch_n;
+  return g;
 }
 
 // Bracket one kernel launch: count it and, when profiling, record events.  Inside
@@ -500,6 +514,7 @@ Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
   L.macro = off; off += align256(42 * 8);
   L.sig0f = off; off += align256((size_t)nphase * 6 * 4);
   L.sig0d = off; off += align256((size_t)nphase * 6 * 8);
+  L.c0 = off; off += align256(32);  // isotropic reference medium (lambda0 + mu0, mu0): 2 double, then 2 float
   L.u64 = off;
   L.rsrc = off;
   if (prec == HS_FP32_REFINED) {
@@ -528,6 +543,7 @@ template <typename T> void fill_march_common(hs_ctx* c, hs::MarchArgs<T>& a) {
   a.partials = c->partials;
   a.st = c->st;
   a.hist = c->hist;
+  a.zstride = c->batch_stride;
 }
 
 template <typename T> void fill_col(hs_ctx* c, hs::ColArgs<T>& a, void* buf, int axis) {
@@ -547,8 +563,15 @@ template <typename T> void fill_col(hs_ctx* c, hs::ColArgs<T>& a, void* buf, int
   a.nh = c->nh;
   a.scale = (T)(2.0 / (double)c->N);
   for (int i = 0; i < 36; ++i) a.G6[i] = (T)c->G6[i];
+  a.c0iso = c->c0_iso ? 1 : 0;
+  a.c0a = (T)c->c0_a;
+  a.c0b = (T)c->c0_b;
+  // an isotropic reference medium is read from the workspace (per item in batched launches),
+  // so captured iteration graphs stay valid when hs_set_material changes it
+  if (c->c0_iso) a.c0dev = (const T*)(c->ws + c->lay.c0 + (sizeof(T) == 8 ? 0 : 16));
   a.st = c->st;
   a.skip_if_done = 1;
+  a.zstride = c->batch_stride;
 }
 
 template <typename T> hs_status launch_force(hs_ctx* c, const double E[6], int in, const float* src) {
@@ -586,10 +609,11 @@ template <typename T> hs_status launch_rows(hs_ctx* c, int mode, double* acc64, 
   a.nrows = 3 * c->n2 * c->n3;
   a.st = c->st;
   a.skip_if_done = skip ? 1 : 0;
+  a.zstride = c->batch_stride;
   cudaError_t e;
   {
     LaunchScope ls(c, acc64 ? HS_K_OTHER : (mode == hs::ROW_C2R ? HS_K_XINV : HS_K_XFWD));
-    e = hs::launch_row<T>(a, mode, c->nblk_row[mode], c->nthr_row, c->smem_row[mode], c->stream);
+    e = hs::launch_row<T>(a, mode, zg(c, dim3(c->nblk_row[mode])), c->nthr_row, c->smem_row[mode], c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_row");
   return HS_OK;
@@ -617,7 +641,7 @@ template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], con
   cudaError_t e;
   {
     LaunchScope ls(c, mode == hs::MODE_FORCE ? (src != nullptr ? HS_K_XPASS_SRC : HS_K_XPASS) : HS_K_FIELDS);
-    e = hs::launch_march<T>(a, c->iso, c->ty, mode, true, c->grid_m, c->nthr_m, sm, c->stream);
+    e = hs::launch_march<T>(a, c->iso, c->ty, mode, true, zg(c, c->grid_m), c->nthr_m, sm, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(real)");
   return HS_OK;
@@ -629,19 +653,19 @@ template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   fill_col<T>(c, a, c->B[buf], 1);
   {
     LaunchScope ls(c, HS_K_YFWD);
-    e = hs::launch_col<T>(a, hs::COL_Y_FWD, c->ct, c->grid_y, c->nthr_y, c->smem_y, c->stream);
+    e = hs::launch_col<T>(a, hs::COL_Y_FWD, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y fwd)");
   fill_col<T>(c, a, c->B[buf], 2);
   {
     LaunchScope ls(c, HS_K_ZGREEN);
-    e = hs::launch_col<T>(a, hs::COL_Z_GREEN, c->ct, c->grid_z, c->nthr_z, c->smem_z, c->stream);
+    e = hs::launch_col<T>(a, hs::COL_Z_GREEN, c->ct, zg(c, c->grid_z), c->nthr_z, c->smem_z, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z green)");
   fill_col<T>(c, a, c->B[buf], 1);
   {
     LaunchScope ls(c, HS_K_YINV);
-    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, c->grid_y, c->nthr_y, c->smem_y, c->stream);
+    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y inv)");
   return HS_OK;
@@ -655,14 +679,14 @@ template <typename T> hs_status launch_state_to_buf(hs_ctx* c, int buf) {
   cudaError_t e;
   {
     LaunchScope ls(c, HS_K_OTHER);
-    e = hs::launch_col<T>(a, hs::COL_Z_INV_STATE, c->ct, c->grid_z, c->nthr_z, c->smem_z, c->stream);
+    e = hs::launch_col<T>(a, hs::COL_Z_INV_STATE, c->ct, zg(c, c->grid_z), c->nthr_z, c->smem_z, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z inv state)");
   fill_col<T>(c, a, c->B[buf], 1);
   a.skip_if_done = 0;
   {
     LaunchScope ls(c, HS_K_OTHER);
-    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, c->grid_y, c->nthr_y, c->smem_y, c->stream);
+    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y inv)");
   return HS_OK;
@@ -860,7 +884,7 @@ hs_status launch_residual64(hs_ctx* c, const double E[6], int mode, void* eps, v
   a.skip_if_done = 0;
   const size_t sm = march_smem(c->n1, c->ty64, true, mode, true);
   LaunchScope ls(c, mode == hs::MODE_FIELDS ? HS_K_FIELDS : HS_K_RESID64);
-  cudaError_t e = hs::launch_march<double>(a, c->iso, c->ty64, mode, true, c->grid_m64, c->nthr_m, sm, c->stream);
+  cudaError_t e = hs::launch_march<double>(a, c->iso, c->ty64, mode, true, zg(c, c->grid_m64), c->nthr_m, sm, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(residual fp64)");
   return HS_OK;
 }
@@ -1057,8 +1081,12 @@ hs_status hs_workspace_size(const int grid[3], int nphase, const hs_options* opt
   return HS_OK;
 }
 
-hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, const double C0[36],
-                    const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+// hs_create with the phase count that sizes the workspace layout given separately
+// (layout_np >= m->nphase; 0: m->nphase): the items of a batched class share one
+// layout, so each is created with the largest phase count of its class.
+static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material* m_in, const double C0[36],
+                             const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                             int layout_np) {
   if (!out || !grid || !m_in || !workspace) return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (m_in->kind == HS_COEFFS_F32) {
@@ -1145,6 +1173,12 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, co
   }
 
   hs_ctx* c = new hs_ctx();
+  {
+    double l0 = 0, m0 = 0;
+    c->c0_iso = is_isotropic(C0v, &l0, &m0);
+    c->c0_a = l0 + m0;
+    c->c0_b = m0;
+  }
   c->n1 = grid[0];
   c->n2 = grid[1];
   c->n3 = grid[2];
@@ -1168,7 +1202,8 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, co
       if (i != k) g += C0v[vidx(j, k) * 6 + vidx(i, l)];
       c->G6[a * 6 + b] = g;
     }
-  c->lay = make_layout(c->n1, c->n2, c->n3, np, o.precision);
+  c->layout_np = std::max(np, layout_np);
+  c->lay = make_layout(c->n1, c->n2, c->n3, c->layout_np, o.precision);
   if (workspace_bytes < c->lay.total) {
     delete c;
     return fail(nullptr, HS_ERR_OOM, "workspace too small");
@@ -1260,6 +1295,21 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, co
     delete c;
     return st;
   }
+  // real-space pass: an automatic row tile is halved while its plane ring does not fit
+  // (FP64 rows of 512 need 2 rows per block)
+  if (o.ytile == 0 && !c->xfuse) {
+    int ty = c->ty;
+    while (ty > 2 && march_smem(c->n1, ty, c->f64, hs::MODE_FORCE, true, true) > (size_t)smem_optin) ty /= 2;
+    if (ty != c->ty && c->n2 % ty == 0) {
+      c->ty = ty;
+      const int yt = c->n2 / c->ty;
+      int nz = std::max(1, std::min(c->n3, (kTargetBlocks + yt - 1) / yt));
+      c->zc = (c->n3 + nz - 1) / nz;
+      if (o.zchunk > 0) c->zc = std::min(o.zchunk, c->n3);
+      nz = (c->n3 + c->zc - 1) / c->zc;
+      c->grid_m = dim3(yt, nz);
+    }
+  }
   // FP64 residual sweep: the widest row tile whose plane ring fits
   c->ty64 = c->ty;
   if (o.precision == HS_FP32_REFINED) {
@@ -1344,7 +1394,19 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, co
           for (int j = i; j < 6; ++j) md[(size_t)p * 21 + k++] = C[i * 6 + j];
       }
     }
-    e = cudaMemcpyAsync(c->matd, md.data(), md.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    {
+      // isotropic reference medium for the Green step of batched launches: (lambda0 + mu0, mu0)
+      // in FP64, then in FP32
+      static_assert(sizeof(float) * 2 + sizeof(double) * 2 <= 32, "c0 region");
+      unsigned char c0b[32] = {0};
+      const double cd[2] = {c->c0_a, c->c0_b};
+      const float cf[2] = {(float)c->c0_a, (float)c->c0_b};
+      memcpy(c0b, cd, sizeof(cd));
+      memcpy(c0b + 16, cf, sizeof(cf));
+      e = cudaMemcpyAsync(c->ws + c->lay.c0, c0b, sizeof(c0b), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->matd, md.data(), md.size() * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) {
       if (c->f64) {
         e = cudaMemcpyAsync(c->matk, md.data(), md.size() * 8, cudaMemcpyHostToDevice, c->stream);
@@ -1400,9 +1462,15 @@ hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, co
   return HS_OK;
 }
 
+hs_status hs_create(hs_ctx** out, const int grid[3], const hs_material* m_in, const double C0[36],
+                    const hs_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+  return create_impl(out, grid, m_in, C0, opt, workspace, workspace_bytes, stream, 0);
+}
+
 hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void* eps_out, void* sig_out,
                    double sig_eff[6], int* iters, double* final_err) {
   if (!c || !E || !sig_eff) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (c->unbound) return fail(c, HS_ERR_INVALID_ARG, "no material: the last hs_set_material failed");
   if (!(tol >= 0) || max_iter < 1) return fail(c, HS_ERR_INVALID_ARG, "bad tol or max_iter");
   double en = 0;
   for (int i = 0; i < 6; ++i) {
@@ -1432,6 +1500,7 @@ hs_status hs_solve(hs_ctx* c, const double E[6], double tol, int max_iter, void*
 hs_status hs_solve_stress(hs_ctx* c, const double S[6], double tol, int max_iter, void* eps_out, void* sig_out,
                           double sig_eff[6], double E_out[6], int* iters, double* final_err) {
   if (!c || !S || !sig_eff) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (c->unbound) return fail(c, HS_ERR_INVALID_ARG, "no material: the last hs_set_material failed");
   if (!(tol >= 0) || max_iter < 1) return fail(c, HS_ERR_INVALID_ARG, "bad tol or max_iter");
   double sn = 0;
   for (int i = 0; i < 6; ++i) {
@@ -1524,6 +1593,65 @@ hs_status hs_set_eigenstrain(hs_ctx* c, const double* eps0) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "eigenstrain upload");
   c->has_eigen = any;
+  return HS_OK;
+}
+
+hs_status hs_create_sized(hs_ctx** out, const int grid[3], const hs_material* m, const double C0[36],
+                          const hs_options* opt, int layout_nphase, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  if (layout_nphase < 1 || layout_nphase > HS_MAX_PHASES)
+    return fail(nullptr, HS_ERR_INVALID_ARG, "layout_nphase out of range");
+  return create_impl(out, grid, m, C0, opt, workspace, workspace_bytes, stream, layout_nphase);
+}
+
+hs_status hs_set_material(hs_ctx* c, const hs_material* m, const double C0[36]) {
+  if (!c || !m) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  if (m->kind != HS_COEFFS_F32 && m->nphase > c->layout_np)
+    return fail(c, HS_ERR_INVALID_ARG, "more phases than the workspace was sized for");
+  const int grid[3] = {c->n1, c->n2, c->n3};
+  // a fresh context on the same workspace, with the same options and layout, uploads the
+  // material and chooses the reference medium; this context takes its material state
+  hs_ctx* t = nullptr;
+  c->unbound = true;
+  hs_status s = create_impl(&t, grid, m, C0, &c->opt, c->ws, c->ws_bytes, c->stream, c->layout_np);
+  if (s != HS_OK) return fail(c, s, std::string("hs_set_material: ") + g_last_error);
+  if (t->layout_np != c->layout_np) {
+    hs_destroy(t);
+    return fail(c, HS_ERR_INVALID_ARG, "more phases than the workspace was sized for");
+  }
+  // captured graphs hold the constitutive-law variant, a general reference medium's
+  // coefficients and the eigenstrain pointer as kernel arguments
+  const bool same_kernels = (t->iso == c->iso) && t->c0_iso && c->c0_iso && !c->has_eigen;
+  if (!same_kernels) drop_graphs(c);
+  c->nphase = t->nphase;
+  c->iso = t->iso;
+  c->table = t->table;
+  memcpy(c->C0, t->C0, sizeof(c->C0));
+  memcpy(c->G6, t->G6, sizeof(c->G6));
+  c->c0_iso = t->c0_iso;
+  c->c0_a = t->c0_a;
+  c->c0_b = t->c0_b;
+  c->has_eigen = false;
+  c->warm = false;
+  c->unbound = false;
+  for (int k = 0; k < HS_K_COUNT; ++k) c->launches[k] += t->launches[k];
+  hs_destroy(t);
+  return HS_OK;
+}
+
+hs_status hs_get_displacement(hs_ctx* c, double* u) {
+  if (!c || !u) return fail(c, HS_ERR_INVALID_ARG, "null argument");
+  cudaError_t e;
+  const size_t n = 3 * c->N;
+  if (c->prec == HS_FP32_REFINED) {
+    e = cudaMemcpyAsync(u, c->u64, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  } else if (c->f64) {
+    e = cudaMemcpyAsync(u, c->B[1], n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    e = hs::launch_f32_to_f64((const float*)c->B[1], u, n, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "displacement export");
   return HS_OK;
 }
 
@@ -1771,6 +1899,526 @@ const char* hs_error_string(hs_status s) {
 const char* hs_last_error(const hs_ctx* c) {
   if (c) return c->last_err.c_str();
   return g_last_error.c_str();
+}
+
+
+// --------------------------------------------------------------------------
+// Batched solves: many RVEs and load cases in shared launches.  Items (an RVE
+// under one macroscopic strain) of the same grid and phase isotropy form a size
+// class; each item has a full single-solve workspace, the items of a class lie
+// one stride apart, and every kernel of the class runs as one launch over all
+// its items (grid.z = item).  A chunk of iterations of every class is captured
+// as one CUDA graph, the classes on forked streams, and replayed until every
+// item has stopped.  Each item keeps its own device status, so an item that
+// converges stops on its own while the others go on.
+// --------------------------------------------------------------------------
+}  // extern "C"
+
+struct hs_batch {
+  struct Class {
+    int n1, n2, n3;
+    bool iso;
+    int max_np;
+    size_t stride;
+    std::vector<int> items;      // item indices in this class, in workspace order
+    std::vector<hs_ctx*> ctx;    // one context per item (ctx[0] drives the batched launches)
+    cudaStream_t s = nullptr;
+    cudaEvent_t joined = nullptr;
+    std::vector<DevStatus> hst;  // host copies of the items' statuses
+  };
+  std::vector<Class> cls;
+  std::vector<int> item_cls, item_pos;
+  int nitem = 0;
+  hs_options opt;
+  bool f64 = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int gchunks[2] = {0, 0};
+  std::vector<std::vector<double>> hist;  // per item: errors (refined: FP64 sweeps; else every evaluation)
+  std::string last_err;
+};
+
+namespace {
+
+hs_status bfail(hs_batch* b, hs_status s, const std::string& msg) {
+  g_last_error = msg;
+  if (b) b->last_err = msg;
+  return s;
+}
+
+struct ClassKey {
+  int n1, n2, n3, iso;
+  bool operator<(const ClassKey& o) const {
+    return std::tie(n1, n2, n3, iso) < std::tie(o.n1, o.n2, o.n3, o.iso);
+  }
+};
+
+// Size classes of a batch, in order of first appearance; stride and bytes per class.
+hs_status batch_classes(int nrve, const int* grids, const hs_material* mats, const int* nphase, int nitem,
+                        const int* item_rve, int prec, std::vector<hs_batch::Class>* out,
+                        std::vector<int>* item_cls, std::vector<int>* item_pos, size_t* total) {
+  if (nrve < 1 || nitem < 1 || !grids || !item_rve) return HS_ERR_INVALID_ARG;
+  std::map<ClassKey, int> index;
+  std::vector<int> rve_iso(nrve);
+  for (int r = 0; r < nrve; ++r) {
+    hs_status s = check_grid(grids + 3 * r);
+    if (s != HS_OK) return s;
+    const int np = mats ? mats[r].nphase : nphase[r];
+    if (np < 1 || np > HS_MAX_PHASES) return HS_ERR_INVALID_ARG;
+    if (mats) {
+      if ((mats[r].kind != HS_IDS_U8 && mats[r].kind != HS_IDS_U16) || !mats[r].ids || !mats[r].table)
+        return HS_ERR_INVALID_ARG;
+      rve_iso[r] = table_isotropic(mats[r].table, np) ? 1 : 0;
+    } else {
+      rve_iso[r] = 0;  // sizing only: isotropy does not change the layout
+    }
+  }
+  out->clear();
+  item_cls->assign(nitem, 0);
+  item_pos->assign(nitem, 0);
+  for (int i = 0; i < nitem; ++i) {
+    const int r = item_rve[i];
+    if (r < 0 || r >= nrve) return HS_ERR_INVALID_ARG;
+    const int* g = grids + 3 * r;
+    const ClassKey k{g[0], g[1], g[2], rve_iso[r]};
+    auto it = index.find(k);
+    int ci;
+    if (it == index.end()) {
+      ci = (int)out->size();
+      index.emplace(k, ci);
+      hs_batch::Class c;
+      c.n1 = g[0];
+      c.n2 = g[1];
+      c.n3 = g[2];
+      c.iso = rve_iso[r] != 0;
+      c.max_np = 0;
+      c.stride = 0;
+      out->push_back(c);
+    } else {
+      ci = it->second;
+    }
+    hs_batch::Class& c = (*out)[ci];
+    (*item_cls)[i] = ci;
+    (*item_pos)[i] = (int)c.items.size();
+    c.items.push_back(i);
+    c.max_np = std::max(c.max_np, mats ? mats[r].nphase : nphase[r]);
+  }
+  size_t off = 0;
+  for (auto& c : *out) {
+    c.stride = align256(make_layout(c.n1, c.n2, c.n3, c.max_np, prec).total);
+    off += c.stride * c.items.size();
+  }
+  *total = off;
+  return HS_OK;
+}
+
+// status records of every item of class c: host copies -> device (reset) or device -> host (read)
+hs_status batch_put_status(hs_batch* b, hs_batch::Class& c) {
+  hs_ctx* L = c.ctx[0];
+  cudaError_t e = cudaMemcpy2DAsync(L->st, c.stride, c.hst.data(), sizeof(DevStatus), sizeof(DevStatus), c.items.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("status upload: ") + cudaGetErrorString(e));
+  return HS_OK;
+}
+
+hs_status batch_get_status(hs_batch* b) {
+  for (auto& c : b->cls) {
+    hs_ctx* L = c.ctx[0];
+    cudaError_t e = cudaMemcpy2DAsync(c.hst.data(), sizeof(DevStatus), L->st, c.stride, sizeof(DevStatus),
+                                      c.items.size(), cudaMemcpyDeviceToHost, b->stream);
+    if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  return HS_OK;
+}
+
+void status_init(DevStatus* h, const hs_ctx* c, double tol, int max_iter, double denom, const double* E, double rel_tol,
+                 bool retired) {
+  memset(h, 0, sizeof(*h));
+  h->max_iter = max_iter;
+  h->hist_cap = kHistCap;
+  h->tol = tol;
+  h->denom = denom;
+  h->nvox = (double)c->N;
+  h->rel_tol = rel_tol;
+  h->retired = retired ? 1 : 0;
+  h->done = retired ? hs::DONE_CONVERGED : hs::DONE_RUNNING;
+  for (int i = 0; i < 6; ++i) h->E[i] = E ? E[i] : 0.0;
+}
+
+hs_status batch_zero_state(hs_batch* b) {
+  for (auto& c : b->cls)
+    for (hs_ctx* x : c.ctx) {
+      cudaError_t e = cudaMemsetAsync(x->S, 0, cbuf_bytes(x), b->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(x->B[0], 0, cbuf_bytes(x), b->stream);
+      if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("state reset: ") + cudaGetErrorString(e));
+    }
+  return HS_OK;
+}
+
+// Run fn(lead) for every class on the class's stream, forked from and joined to
+// the batch stream (so classes overlap on the device).
+template <typename F> hs_status batch_fork(hs_batch* b, F fn) {
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("fork: ") + cudaGetErrorString(e));
+  for (auto& c : b->cls) {
+    hs_ctx* L = c.ctx[0];
+    e = cudaStreamWaitEvent(c.s, b->fork, 0);
+    if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("fork: ") + cudaGetErrorString(e));
+    cudaStream_t keep = L->stream;
+    L->stream = c.s;
+    hs_status st = fn(L);
+    L->stream = keep;
+    if (st != HS_OK) return bfail(b, st, L->last_err);
+    e = cudaEventRecord(c.joined, c.s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, c.joined, 0);
+    if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("join: ") + cudaGetErrorString(e));
+  }
+  return HS_OK;
+}
+
+void batch_drop_graph(hs_batch* b, int gi) {
+  if (b->gexec[gi]) cudaGraphExecDestroy(b->gexec[gi]);
+  b->gexec[gi] = nullptr;
+  for (auto& c : b->cls) drop_graph(c.ctx[0], gi, false);
+}
+
+// Basic-scheme iterations of every item until every item's status says done.
+template <typename T> hs_status batch_iterate(hs_batch* b, bool with_src) {
+  const int gi = with_src ? 1 : 0;
+  const int chunk = std::max(1, b->opt.check_every);
+  const double zeroE[6] = {0, 0, 0, 0, 0, 0};
+  auto one_chunk = [&](hs_ctx* L) -> hs_status {
+    for (int i = 0; i < chunk; ++i) {
+      hs_status s = launch_rows<T>(L, hs::ROW_C2R, nullptr, true);
+      if (s == HS_OK) s = launch_stencil<T>(L, zeroE, with_src ? L->rsrc : nullptr, hs::MODE_FORCE, nullptr, nullptr);
+      if (s == HS_OK) s = launch_rows<T>(L, hs::ROW_R2C, nullptr, true);
+      if (s == HS_OK) s = launch_cols<T>(L, 0);
+      if (s != HS_OK) return s;
+    }
+    return HS_OK;
+  };
+  const bool graphs = b->opt.use_graphs && b->stream != nullptr && b->stream != cudaStreamLegacy &&
+                      b->stream != cudaStreamPerThread;
+  for (;;) {
+    if (graphs && b->gexec[gi] != nullptr) {
+      cudaError_t e = cudaGraphLaunch(b->gexec[gi], b->stream);
+      if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+      for (auto& c : b->cls) account_replay(c.ctx[0], gi);
+    } else if (graphs && b->gchunks[gi] >= 1) {
+      batch_drop_graph(b, gi);
+      cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+      for (auto& c : b->cls) {
+        c.ctx[0]->capturing = true;
+        c.ctx[0]->cap_gi = gi;
+      }
+      hs_status s = batch_fork(b, one_chunk);
+      for (auto& c : b->cls) c.ctx[0]->capturing = false;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(b->stream, &g);
+      cudaGraphExec_t ex = nullptr;
+      if (s == HS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (s != HS_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        batch_drop_graph(b, gi);
+        return s != HS_OK ? s : bfail(b, HS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      }
+      b->gexec[gi] = ex;
+      e = cudaGraphLaunch(ex, b->stream);
+      if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+      for (auto& c : b->cls) account_replay(c.ctx[0], gi);
+    } else {
+      hs_status s = batch_fork(b, one_chunk);
+      if (s != HS_OK) return s;
+      ++b->gchunks[gi];
+    }
+    hs_status s = batch_get_status(b);
+    if (s != HS_OK) return s;
+    bool all = true;
+    for (auto& c : b->cls)
+      for (auto& h : c.hst)
+        if (!h.retired && !h.done) all = false;
+    if (all) return HS_OK;
+  }
+}
+
+// u64 += inverse transform of every item's correction state (refined mode)
+hs_status batch_accumulate(hs_batch* b) {
+  return batch_fork(b, [&](hs_ctx* L) -> hs_status {
+    hs_status s = launch_state_to_buf<float>(L, 0);
+    if (s == HS_OK) s = launch_rows<float>(L, hs::ROW_C2R, L->u64, false);
+    return s;
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_status hs_batch_workspace_size(int nrve, const int* grids, const int* nphase, int nitem, const int* item_rve,
+                                  const hs_options* opt, size_t* bytes) {
+  if (!grids || !nphase || !item_rve || !bytes) return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
+  hs_options o;
+  hs_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED) return fail(nullptr, HS_ERR_INVALID_ARG, "bad precision");
+  std::vector<hs_batch::Class> cls;
+  std::vector<int> ic, ip;
+  size_t total = 0;
+  hs_status s = batch_classes(nrve, grids, nullptr, nphase, nitem, item_rve, o.precision, &cls, &ic, &ip, &total);
+  if (s != HS_OK) return fail(nullptr, s, "bad batch description");
+  *bytes = total;
+  return HS_OK;
+}
+
+hs_status hs_batch_create(hs_batch** out, int nrve, const int* grids, const hs_material* mats, int nitem,
+                          const int* item_rve, const hs_options* opt, int autotune, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  if (!out || !grids || !mats || !item_rve || !workspace) return fail(nullptr, HS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(nullptr, HS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  hs_options o;
+  hs_default_options(&o);
+  if (opt) o = *opt;
+  if (o.xfuse != 0) return fail(nullptr, HS_ERR_INVALID_ARG, "batched solves run the split x-pass (xfuse = 0)");
+  if (o.precision < HS_FP64 || o.precision > HS_FP32_REFINED) return fail(nullptr, HS_ERR_INVALID_ARG, "bad precision");
+  hs_batch* b = new hs_batch();
+  size_t total = 0;
+  hs_status s = batch_classes(nrve, grids, mats, nullptr, nitem, item_rve, o.precision, &b->cls, &b->item_cls,
+                              &b->item_pos, &total);
+  if (s != HS_OK) {
+    delete b;
+    return fail(nullptr, s, "bad batch description (grid, material kind, phase count or item index)");
+  }
+  if (workspace_bytes < total) {
+    delete b;
+    return fail(nullptr, HS_ERR_OOM, "workspace too small for the batch");
+  }
+  b->nitem = nitem;
+  b->opt = o;
+  b->f64 = (o.precision == HS_FP64);
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->hist.assign(nitem, {});
+  auto undo = [&](hs_status st, const std::string& msg) {
+    hs_batch_destroy(b);
+    return fail(nullptr, st, msg);
+  };
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return undo(HS_ERR_CUDA, "event create");
+  char* base = static_cast<char*>(workspace);
+  for (auto& c : b->cls) {
+    if (cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.joined, cudaEventDisableTiming) != cudaSuccess)
+      return undo(HS_ERR_CUDA, "stream create");
+    hs_options oc = o;
+    const int grid[3] = {c.n1, c.n2, c.n3};
+    if (autotune) {
+      // the class's tiling from the plan cache (tuned on the class's first workspace on a miss)
+      hs_options best;
+      const hs_material& m0 = mats[item_rve[c.items[0]]];
+      if (hs_autotune(grid, &m0, &o, base, c.stride, stream, 8, &best, nullptr) == HS_OK) oc = best;
+    }
+    for (size_t k = 0; k < c.items.size(); ++k) {
+      hs_ctx* x = nullptr;
+      const int r = item_rve[c.items[k]];
+      s = create_impl(&x, grid, &mats[r], nullptr, &oc, base + k * c.stride, c.stride, stream, c.max_np);
+      if (s != HS_OK) return undo(s, std::string("item ") + std::to_string(c.items[k]) + ": " + g_last_error);
+      if (x->iso != c.iso || !x->c0_iso) {
+        hs_destroy(x);
+        return undo(HS_ERR_INVALID_ARG, "batched items need an isotropic reference medium");
+      }
+      c.ctx.push_back(x);
+    }
+    c.ctx[0]->batch_n = (int)c.items.size();
+    c.ctx[0]->batch_stride = c.stride;
+    c.hst.resize(c.items.size());
+    base += c.stride * c.items.size();
+  }
+  *out = b;
+  return HS_OK;
+}
+
+hs_status hs_batch_solve(hs_batch* b, const double* E, double tol, int max_iter, double* sig_eff, int* iters,
+                         double* final_err, int* status) {
+  if (!b || !E || !sig_eff || !iters || !final_err || !status) return bfail(b, HS_ERR_INVALID_ARG, "null argument");
+  if (!(tol >= 0) || max_iter < 1) return bfail(b, HS_ERR_INVALID_ARG, "bad tol or max_iter");
+  for (int i = 0; i < b->nitem; ++i) {
+    double en = 0;
+    for (int k = 0; k < 6; ++k) {
+      if (!std::isfinite(E[6 * i + k])) return bfail(b, HS_ERR_INVALID_ARG, "non-finite E");
+      en += E[6 * i + k] * E[6 * i + k];
+    }
+    if (en == 0) return bfail(b, HS_ERR_INVALID_ARG, "E = 0 (the error norm would divide by <sigma> = 0)");
+  }
+  b->last_err.clear();
+  for (auto& h : b->hist) h.clear();
+  const int n = b->nitem;
+  std::vector<int> total(n, 0), done(n, 0);
+  std::vector<hs_status> st(n, HS_NOT_CONVERGED);
+  auto item_status = [&](int i) -> DevStatus& { return b->cls[b->item_cls[i]].hst[b->item_pos[i]]; };
+  auto item_ctx = [&](int i) -> hs_ctx* { return b->cls[b->item_cls[i]].ctx[b->item_pos[i]]; };
+  auto finish = [&](int i, const DevStatus& h, hs_status s) {
+    for (int k = 0; k < 6; ++k) sig_eff[6 * i + k] = h.sig_mean[k];
+    final_err[i] = h.err;
+    st[i] = s;
+    done[i] = 1;
+  };
+  hs_status s;
+  if (b->opt.precision != HS_FP32_REFINED) {
+    for (int i = 0; i < n; ++i) status_init(&item_status(i), item_ctx(i), tol, max_iter, 0.0, E + 6 * i, 0.0, false);
+    for (auto& c : b->cls)
+      if ((s = batch_put_status(b, c)) != HS_OK) return s;
+    if ((s = batch_zero_state(b)) != HS_OK) return s;
+    s = b->f64 ? batch_iterate<double>(b, false) : batch_iterate<float>(b, false);
+    if (s != HS_OK) return s;
+    for (int i = 0; i < n; ++i) {
+      const DevStatus& h = item_status(i);
+      total[i] = h.evals;
+      finish(i, h, status_code(h));
+      hs_ctx* x = item_ctx(i);
+      const int k = std::min(h.evals, kHistCap);
+      b->hist[i].resize(k);
+      if (k) {
+        cudaError_t e = cudaMemcpyAsync(b->hist[i].data(), x->hist, k * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, "history read");
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, "history read");
+  } else {
+    // FP32 iterations with FP64 residual sweeps, every item in step: first the plain FP32
+    // solve from u = 0 (the correction equation of u = 0 is the problem itself), then
+    // alternately an FP64 sweep (which takes every stop decision) and an FP32 correction solve.
+    const double zeroE[6] = {0, 0, 0, 0, 0, 0};
+    for (auto& c : b->cls)
+      for (hs_ctx* x : c.ctx) {
+        cudaError_t e = cudaMemsetAsync(x->u64, 0, 3 * x->N * sizeof(double), b->stream);
+        if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, "u64 reset");
+      }
+    if (max_iter > 1) {
+      const int budget = std::min(std::max(1, b->opt.inner_max), max_iter - 1);
+      for (int i = 0; i < n; ++i)
+        status_init(&item_status(i), item_ctx(i), 0.0, budget, 0.0, E + 6 * i, b->opt.inner_ratio, false);
+      for (auto& c : b->cls)
+        if ((s = batch_put_status(b, c)) != HS_OK) return s;
+      if ((s = batch_zero_state(b)) != HS_OK) return s;
+      if ((s = batch_iterate<float>(b, false)) != HS_OK) return s;
+      for (int i = 0; i < n; ++i) {
+        const DevStatus& h = item_status(i);
+        total[i] += h.evals;
+        if (h.done == hs::DONE_DIVERGED) finish(i, h, HS_DIVERGED);
+      }
+      for (int i = 0; i < n; ++i) item_status(i).retired = done[i];
+      for (auto& c : b->cls)
+        if ((s = batch_put_status(b, c)) != HS_OK) return s;
+      if ((s = batch_accumulate(b)) != HS_OK) return s;
+    }
+    for (;;) {
+      for (int i = 0; i < n; ++i)
+        status_init(&item_status(i), item_ctx(i), 0.0, 1 << 30, 0.0, E + 6 * i, 0.0, done[i] != 0);
+      for (auto& c : b->cls)
+        if ((s = batch_put_status(b, c)) != HS_OK) return s;
+      s = batch_fork(b, [&](hs_ctx* L) { return launch_residual64(L, zeroE, hs::MODE_FORCE, nullptr, nullptr); });
+      if (s != HS_OK) return s;
+      if ((s = batch_get_status(b)) != HS_OK) return s;
+      bool any = false;
+      for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        const DevStatus& h = item_status(i);
+        total[i] += 1;
+        b->hist[i].push_back(h.err);
+        if (!(h.err == h.err) || h.err > 1e300) finish(i, h, HS_DIVERGED);
+        else if (h.err < tol) finish(i, h, HS_OK);
+        else if (total[i] >= max_iter) finish(i, h, HS_NOT_CONVERGED);
+        else any = true;
+      }
+      if (!any) break;
+      // correction solves K du = -r in FP32 (source r, macro strain 0) for the items still running
+      std::vector<double> err64(n), norm64(n);
+      for (int i = 0; i < n; ++i) {
+        err64[i] = item_status(i).err;
+        norm64[i] = item_status(i).sig_norm;
+      }
+      for (int i = 0; i < n; ++i) {
+        const int budget = std::min(std::max(1, b->opt.inner_max), std::max(1, max_iter - total[i]));
+        status_init(&item_status(i), item_ctx(i), b->opt.inner_ratio * err64[i], budget, norm64[i], zeroE, 0.0,
+                    done[i] != 0);
+      }
+      for (auto& c : b->cls)
+        if ((s = batch_put_status(b, c)) != HS_OK) return s;
+      if ((s = batch_zero_state(b)) != HS_OK) return s;
+      if ((s = batch_iterate<float>(b, true)) != HS_OK) return s;
+      for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        const DevStatus& h = item_status(i);
+        total[i] += h.evals;
+        if (h.done == hs::DONE_DIVERGED) finish(i, h, HS_DIVERGED);
+      }
+      for (int i = 0; i < n; ++i) item_status(i).retired = done[i];
+      for (auto& c : b->cls)
+        if ((s = batch_put_status(b, c)) != HS_OK) return s;
+      if ((s = batch_accumulate(b)) != HS_OK) return s;
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, HS_ERR_CUDA, "batch sync");
+  }
+  bool all_ok = true;
+  for (int i = 0; i < n; ++i) {
+    iters[i] = total[i];
+    status[i] = st[i];
+    if (st[i] != HS_OK) all_ok = false;
+  }
+  return all_ok ? HS_OK : HS_NOT_CONVERGED;
+}
+
+hs_status hs_batch_err_history(const hs_batch* b, int item, double* out, int n, int* n_written) {
+  if (!b || item < 0 || item >= b->nitem || (!out && n > 0) || n < 0) return HS_ERR_INVALID_ARG;
+  const auto& h = b->hist[item];
+  const int k = std::min(n, (int)h.size());
+  for (int i = 0; i < k; ++i) out[i] = h[i];
+  if (n_written) *n_written = k;
+  return HS_OK;
+}
+
+hs_status hs_batch_launches(hs_batch* b, long long* launches) {
+  if (!b || !launches) return HS_ERR_INVALID_ARG;
+  long long n = 0;
+  for (auto& c : b->cls)
+    for (hs_ctx* x : c.ctx)
+      for (int k = 0; k < HS_K_COUNT; ++k) {
+        n += x->launches[k];
+        x->launches[k] = 0;
+      }
+  *launches = n;
+  return HS_OK;
+}
+
+hs_status hs_batch_classes(const hs_batch* b, int* nclass, int* class_of_item) {
+  if (!b || !nclass) return HS_ERR_INVALID_ARG;
+  *nclass = (int)b->cls.size();
+  if (class_of_item)
+    for (int i = 0; i < b->nitem; ++i) class_of_item[i] = b->item_cls[i];
+  return HS_OK;
+}
+
+const char* hs_batch_last_error(const hs_batch* b) { return b ? b->last_err.c_str() : g_last_error.c_str(); }
+
+void hs_batch_destroy(hs_batch* b) {
+  if (!b) return;
+  for (int gi = 0; gi < 2; ++gi)
+    if (b->gexec[gi]) cudaGraphExecDestroy(b->gexec[gi]);
+  for (auto& c : b->cls) {
+    for (hs_ctx* x : c.ctx) hs_destroy(x);
+    if (c.s) cudaStreamDestroy(c.s);
+    if (c.joined) cudaEventDestroy(c.joined);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
 }
 
 }  // extern "C"

@@ -34,12 +34,33 @@ template <typename T> struct ColArgs {
   int n1, n2, n3, P, nh;
   T scale;           // 2/N
   T G6[36];          // Omega^-1 (Voigt pairs) = G6 . M (Voigt pairs)
+  // isotropic reference medium: Omega^-1 = c0a M + c0b tr(M) I with c0a = lambda0 + mu0,
+  // c0b = mu0 (used when c0iso != 0, or always when c0dev is given)
+  int c0iso;
+  T c0a, c0b;
+  const T* c0dev;    // not null: (c0a, c0b) read here (per item in batched launches)
   const DevStatus* st;
   int skip_if_done;
+  size_t zstride;    // batched launches: bytes between the workspaces of consecutive items
 };
 
+template <typename T> __device__ __forceinline__ ColArgs<T> col_item_args(const ColArgs<T>& a) {
+  if (a.zstride == 0) return a;
+  ColArgs<T> b = a;
+  const size_t o = (size_t)blockIdx.z * a.zstride;
+  b.buf = zshift(a.buf, o);
+  b.S = zshift(a.S, o);
+  b.tw = zshift(a.tw, o);
+  b.tw1 = zshift(a.tw1, o);
+  b.tw2 = zshift(a.tw2, o);
+  b.tw3 = zshift(a.tw3, o);
+  b.c0dev = zshift(a.c0dev, o);
+  b.st = zshift(a.st, o);
+  return b;
+}
+
 template <typename T>
-__device__ __forceinline__ void green_apply(const ColArgs<T>& a, int h1, int h2, int h3,
+__device__ __forceinline__ void green_apply(const ColArgs<T>& a, T c0a, T c0b, bool c0iso, int h1, int h2, int h3,
                                             typename cplx_t<T>::type (&F)[3],
                                             typename cplx_t<T>::type (&U)[3]) {
   using C = typename cplx_t<T>::type;
@@ -67,12 +88,19 @@ __device__ __forceinline__ void green_apply(const ColArgs<T>& a, int h1, int h2,
   M[4] = T(2) * (D[0].x * D[2].x + D[0].y * D[2].y);
   M[5] = T(2) * (D[0].x * D[1].x + D[0].y * D[1].y);
   T A[6];
+  if (c0iso) {
+    // Omega^-1_jl = sum_ik lambda0_jikl M_ik = (lambda0 + mu0) M_jl + mu0 tr(M) delta_jl
+    const T tr = c0b * (M[0] + M[1] + M[2]);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    T s = 0;
+    for (int i = 0; i < 6; ++i) A[i] = c0a * M[i] + (i < 3 ? tr : T(0));
+  } else {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) s += a.G6[i * 6 + j] * M[j];
-    A[i] = s;
+    for (int i = 0; i < 6; ++i) {
+      T s = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += a.G6[i * 6 + j] * M[j];
+      A[i] = s;
+    }
   }
   // inverse of the symmetric 3x3 [[A0,A5,A4],[A5,A1,A3],[A4,A3,A2]]
   const T c11 = A[1] * A[2] - A[3] * A[3];
@@ -103,6 +131,9 @@ template <typename T, int CT>
 __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T>::type* sm, size_t base,
                                           size_t rstride, size_t cstride, int x0, int outer, int ncol, int L,
                                           int tid, int nthr) {
+  const bool c0iso = a.c0iso || a.c0dev != nullptr;
+  const T c0a = a.c0dev != nullptr ? a.c0dev[0] : a.c0a;
+  const T c0b = a.c0dev != nullptr ? a.c0dev[1] : a.c0b;
   using C = typename cplx_t<T>::type;
   constexpr int W = 3 * CT;
   constexpr int GU = 4;  // points per thread per batch: state loads issued together
@@ -126,7 +157,7 @@ __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T
         C F[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) F[c] = sm[z * W + c * CT + col];
-        green_apply<T>(a, x0 + col, outer, z, F, U[u]);
+        green_apply<T>(a, c0a, c0b, c0iso, x0 + col, outer, z, F, U[u]);
         const size_t g = base + z * rstride + col;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -142,9 +173,10 @@ __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T
 // fixed at compile time (hot sizes); LF = 0: both taken at run time; LF = -1:
 // run time, plans with a radix-5, 7 or 11 stage.
 template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArgs<T> a_) {
   using C = typename cplx_t<T>::type;
-  if (a.skip_if_done && a.st->done) return;
+  const ColArgs<T> a = col_item_args(a_);
+  if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);  // [L][3][CT]
   const bool yaxis = (MODE == COL_Y_FWD || MODE == COL_Y_INV);

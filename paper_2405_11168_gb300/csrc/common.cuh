@@ -16,7 +16,7 @@ struct DevStatus {
   int max_iter;   // stop (done = 2) after this many evaluations
   int hist_cap;   // capacity of the error history
   unsigned int counter;  // block-arrival counter of the last-block reduction
-  int pad0;
+  int retired;    // batched solves: this item is finished and every kernel skips it
   double tol;       // converged when err < tol
   double err;       // error of the last evaluation, Eq. (tolerance)
   double l2;        // L2 norm of the nodal force, Eq. (L2-norm)
@@ -39,6 +39,14 @@ struct DevStatus {
 };
 
 enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
+
+// Batched launches (one launch over many solves of the same grid): item
+// blockIdx.z works in the workspace that starts zstride bytes after item
+// blockIdx.z - 1's, so every workspace pointer of the launch moves by
+// blockIdx.z * zstride.  zstride = 0: a single solve.
+template <typename P> __device__ __forceinline__ P* zshift(P* p, size_t off) {
+  return p == nullptr ? p : reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(p) + off);
+}
 constexpr int NRED = 7;  // sum of sigma^T1 + sigma^T2 (6), sum |F|^2 (1)
 
 // Isotropic phases: per phase (lambda, mu).

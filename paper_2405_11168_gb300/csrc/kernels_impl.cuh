@@ -173,7 +173,7 @@ static cudaError_t col_dispatch(const ColArgs<T>& a, int mode, dim3 g, int nthr,
 }
 
 template <typename T, int MODE, int LF = 0>
-static cudaError_t row_one(const RowArgs<T>& a, int nb, int nthr, size_t smem, cudaStream_t s) {
+static cudaError_t row_one(const RowArgs<T>& a, dim3 nb, int nthr, size_t smem, cudaStream_t s) {
   auto k = k_row<T, MODE, LF>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -202,7 +202,7 @@ static cudaError_t row_occ(int n1, int nthr, size_t smem, int* n) {
 
 // compile-time variants for 256-thread blocks at the hot lengths
 template <typename T, int MODE>
-static cudaError_t row_dispatch(const RowArgs<T>& a, int nb, int nthr, size_t smem, cudaStream_t s) {
+static cudaError_t row_dispatch(const RowArgs<T>& a, dim3 nb, int nthr, size_t smem, cudaStream_t s) {
   if (nthr == 256) {
     if (a.n1 == 256) return row_one<T, MODE, 256>(a, nb, nthr, smem, s);
     if (a.n1 == 512) return row_one<T, MODE, 512>(a, nb, nthr, smem, s);
@@ -269,7 +269,7 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     return cudaErrorInvalidValue;                                                                        \
   }                                                                                                      \
   template <>                                                                                            \
-  cudaError_t launch_row<T>(const RowArgs<T>& a, int mode, int nb, int nthr, size_t smem, cudaStream_t s) { \
+  cudaError_t launch_row<T>(const RowArgs<T>& a, int mode, dim3 nb, int nthr, size_t smem, cudaStream_t s) { \
     if (a.tw == nullptr || (mode == ROW_C2R ? (a.spec_in == nullptr || (a.real_out == nullptr && a.acc64 == nullptr)) \
                                             : (a.real_in == nullptr || a.spec_out == nullptr)))         \
       return cudaErrorInvalidValue;                                                                      \
@@ -308,7 +308,7 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     return col_ct<T, CT, -1>(a, mode, grid, nthr, smem, s);                                              \
   }                                                                                                      \
   template <>                                                                                            \
-  cudaError_t launch_row_ext<T>(const RowArgs<T>& a, int mode, int nb, int nthr, size_t smem, cudaStream_t s) { \
+  cudaError_t launch_row_ext<T>(const RowArgs<T>& a, int mode, dim3 nb, int nthr, size_t smem, cudaStream_t s) { \
     return mode == ROW_C2R ? row_one<T, ROW_C2R, -1>(a, nb, nthr, smem, s)                               \
                            : row_one<T, ROW_R2C, -1>(a, nb, nthr, smem, s);                              \
   }                                                                                                      \

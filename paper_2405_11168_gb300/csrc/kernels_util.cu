@@ -21,6 +21,16 @@ cudaError_t launch_ids_u8_to_u16(const uint8_t* in, uint16_t* out, size_t n, cud
   return cudaGetLastError();
 }
 
+__global__ void k_f32_to_f64(const float* in, double* out, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s) {
+  k_f32_to_f64<<<1024, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_max_id(const uint16_t* ids, size_t n, int* out, cudaStream_t s) {
   k_max_id<<<1024, 256, 0, s>>>(ids, n, out);
   return cudaGetLastError();

@@ -19,15 +19,15 @@ cudaError_t launch_march(const MarchArgs<T>& a, bool iso, int ty, int mode, bool
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
 
-// mode: ROW_C2R / ROW_R2C
+// mode: ROW_C2R / ROW_R2C; grid.x persistent blocks per item, grid.z items (batched launches)
 template <typename T>
-cudaError_t launch_row(const RowArgs<T>& a, int mode, int nblocks, int nthr, size_t smem, cudaStream_t s);
+cudaError_t launch_row(const RowArgs<T>& a, int mode, dim3 grid, int nthr, size_t smem, cudaStream_t s);
 
 // the same passes for plans with a radix-5, 7 or 11 stage (default column tile only)
 template <typename T>
 cudaError_t launch_col_ext(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
 template <typename T>
-cudaError_t launch_row_ext(const RowArgs<T>& a, int mode, int nblocks, int nthr, size_t smem, cudaStream_t s);
+cudaError_t launch_row_ext(const RowArgs<T>& a, int mode, dim3 grid, int nthr, size_t smem, cudaStream_t s);
 template <typename T>
 cudaError_t row_blocks_per_sm_ext(int mode, int nthr, size_t smem, int* n);
 
@@ -37,6 +37,8 @@ cudaError_t row_blocks_per_sm(int mode, int n1, int nthr, size_t smem, int* n);
 
 // u8 phase ids -> u16
 cudaError_t launch_ids_u8_to_u16(const uint8_t* in, uint16_t* out, size_t n, cudaStream_t s);
+// widen a float array to double
+cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
 // largest id into *out (int, must start at 0)
 cudaError_t launch_max_id(const uint16_t* ids, size_t n, int* out, cudaStream_t s);
 // padded T-complex state <-> packed complex128 [3][n3][n2][nh]

@@ -56,7 +56,31 @@ template <typename T> struct MarchArgs {
   int skip_if_done;
   const double* Edev;    // not null: the macroscopic strain is read here (applied-stress control)
   const T* sig0;         // not null: lambda(ph) : eps0(ph) per phase, Voigt [nphase][6] (eigenstrain)
+  size_t zstride;        // batched launches: bytes between the workspaces of consecutive items
+                         // (eps_out and sig_out do not move: batched launches write no fields)
 };
+
+// The arguments of item blockIdx.z of a batched launch (every workspace pointer moved).
+template <typename T> __device__ __forceinline__ MarchArgs<T> march_item_args(const MarchArgs<T>& a) {
+  if (a.zstride == 0) return a;
+  MarchArgs<T> b = a;
+  const size_t o = (size_t)blockIdx.z * a.zstride;
+  b.in = zshift(a.in, o);
+  b.out = zshift(a.out, o);
+  b.ids = zshift(a.ids, o);
+  b.mat = zshift(a.mat, o);
+  b.tw1 = zshift(a.tw1, o);
+  b.partials = zshift(a.partials, o);
+  b.st = zshift(a.st, o);
+  b.hist = zshift(a.hist, o);
+  b.src = zshift(a.src, o);
+  b.u64 = zshift(a.u64, o);
+  b.ureal = zshift(a.ureal, o);
+  b.fout = zshift(a.fout, o);
+  b.Edev = zshift(a.Edev, o);
+  b.sig0 = zshift(a.sig0, o);
+  return b;
+}
 
 // Macroscopic strain of this evaluation: the kernel parameter, or the device
 // copy that the applied-stress loop updates.
@@ -319,13 +343,16 @@ __device__ __forceinline__ T march_u(const typename cplx_t<T>::type* ring, const
 }
 
 template <typename T, int TY, class MAT, int MODE, bool REAL>
-__global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a, const MAT mat) {
+__global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a_, const MAT mat_) {
   using C = typename cplx_t<T>::type;
   constexpr int NR = TY + 2;          // corner rows per plane (1 halo row each side)
   constexpr int NSI = 3 * NR / 2;     // packed complex sequences per plane
   constexpr int NSF = 3 * TY / 2;     // packed sequences of the output force
   constexpr int EPC = 16 / (int)sizeof(C);
-  if (a.skip_if_done && a.st->done) return;
+  const MarchArgs<T> a = march_item_args(a_);
+  MAT mat = mat_;
+  mat.tab = a.mat;
+  if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3, P = a.P, nh = n1 / 2 + 1;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;

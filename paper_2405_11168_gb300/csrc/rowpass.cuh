@@ -31,7 +31,22 @@ template <typename T> struct RowArgs {
   int n1, P, nrows;
   const DevStatus* st;
   int skip_if_done;
+  size_t zstride;     // batched launches: bytes between the workspaces of consecutive items
 };
+
+template <typename T> __device__ __forceinline__ RowArgs<T> row_item_args(const RowArgs<T>& a) {
+  if (a.zstride == 0) return a;
+  RowArgs<T> b = a;
+  const size_t o = (size_t)blockIdx.z * a.zstride;
+  b.spec_in = zshift(a.spec_in, o);
+  b.spec_out = zshift(a.spec_out, o);
+  b.real_in = zshift(a.real_in, o);
+  b.real_out = zshift(a.real_out, o);
+  b.acc64 = zshift(a.acc64, o);
+  b.tw = zshift(a.tw, o);
+  b.st = zshift(a.st, o);
+  return b;
+}
 
 __device__ __forceinline__ void group_sync(bool wsync) {
   if (wsync) __syncwarp();
@@ -92,9 +107,10 @@ __device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& 
 // sizes); LF = 0: both taken at run time; LF = -1: run time, plans with a
 // radix-5, 7 or 11 stage.
 template <typename T, int MODE, int LF = 0>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowArgs<T> a_) {
   using C = typename cplx_t<T>::type;
-  if (a.skip_if_done && a.st->done) return;
+  const RowArgs<T> a = row_item_args(a_);
+  if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = LF > 0 ? LF : a.n1, P = a.P, nh = n1 / 2 + 1, half = n1 / 2;
   const int tid = threadIdx.x, nthr = LF > 0 ? 256 : (int)blockDim.x;

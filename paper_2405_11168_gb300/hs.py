@@ -49,6 +49,17 @@ EXPORTS = [
     "hs_profile_read",
     "hs_residual_noalloc",
     "hs_compress_coefficients",
+    "hs_create_sized",
+    "hs_set_material",
+    "hs_get_displacement",
+    "hs_batch_workspace_size",
+    "hs_batch_create",
+    "hs_batch_solve",
+    "hs_batch_err_history",
+    "hs_batch_launches",
+    "hs_batch_classes",
+    "hs_batch_last_error",
+    "hs_batch_destroy",
     "hs_destroy",
     "hs_error_string",
     "hs_last_error",
@@ -96,6 +107,10 @@ def load(path: str = LIB_PATH):
     lib.hs_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
                               dptr, ctypes.POINTER(hs_options), P, ctypes.c_size_t, P]
     lib.hs_solve.argtypes = [P, dptr, D, I, P, P, dptr, iptr, dptr]
+    lib.hs_create_sized.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
+                                    dptr, ctypes.POINTER(hs_options), I, P, ctypes.c_size_t, P]
+    lib.hs_set_material.argtypes = [P, ctypes.POINTER(hs_material), dptr]
+    lib.hs_get_displacement.argtypes = [P, P]
     lib.hs_autotune.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hs_material),
                                 ctypes.POINTER(hs_options), P, ctypes.c_size_t, P, I,
                                 ctypes.POINTER(hs_options), dptr]
@@ -109,6 +124,18 @@ def load(path: str = LIB_PATH):
     lib.hs_profile_read.argtypes = [P, dptr, ctypes.POINTER(ctypes.c_longlong)]
     lib.hs_residual_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), P, dptr, I, dptr, P, P, dptr, dptr, P]
     lib.hs_compress_coefficients.argtypes = [ctypes.POINTER(ctypes.c_int), P, P, dptr, I, iptr]
+    lib.hs_batch_workspace_size.argtypes = [I, iptr, iptr, I, iptr, ctypes.POINTER(hs_options),
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    lib.hs_batch_create.argtypes = [ctypes.POINTER(P), I, iptr, ctypes.POINTER(hs_material), I, iptr,
+                                    ctypes.POINTER(hs_options), I, P, ctypes.c_size_t, P]
+    lib.hs_batch_solve.argtypes = [P, dptr, D, I, dptr, iptr, dptr, iptr]
+    lib.hs_batch_err_history.argtypes = [P, I, dptr, I, iptr]
+    lib.hs_batch_launches.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hs_batch_classes.argtypes = [P, iptr, iptr]
+    lib.hs_batch_last_error.argtypes = [P]
+    lib.hs_batch_last_error.restype = ctypes.c_char_p
+    lib.hs_batch_destroy.argtypes = [P]
+    lib.hs_batch_destroy.restype = None
     lib.hs_destroy.argtypes = [P]
     lib.hs_destroy.restype = None
     lib.hs_error_string.argtypes = [I]
@@ -116,7 +143,7 @@ def load(path: str = LIB_PATH):
     lib.hs_last_error.argtypes = [P]
     lib.hs_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("hs_destroy", "hs_error_string", "hs_last_error"):
+        if name not in ("hs_destroy", "hs_error_string", "hs_last_error", "hs_batch_destroy", "hs_batch_last_error"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -227,10 +254,13 @@ def autotune(ids, table, precision=HS_FP32, iters=8, device="cuda", stream=None,
 class Solver:
     """One microstructure on one device (thin wrapper over hs_create / hs_solve)."""
 
-    def __init__(self, ids, table, C0=None, precision=HS_FP64, device="cuda", stream=None, coeffs=None, **optkw):
+    def __init__(self, ids, table, C0=None, precision=HS_FP64, device="cuda", stream=None, coeffs=None,
+                 layout_nphase=None, **optkw):
         """ids [N3][N2][N1] and table [nphase][6][6]; or ids = table = None and ``coeffs``, the full
         stiffness of every voxel as [21][N3][N2][N1] float32 (upper triangles, host array or
-        device tensor), which the library stores exactly as phases."""
+        device tensor), which the library stores exactly as phases.  ``layout_nphase``: size the
+        workspace for this many phases (hs_create_sized), so that set_material can bind any
+        material of up to that many phases later."""
         import torch
 
         self.lib = load()
@@ -250,7 +280,8 @@ class Solver:
         else:
             table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
             self.nphase = table.shape[0]
-        nbytes = workspace_size(self.grid, self.nphase, self.opt)
+        self.layout_nphase = max(self.nphase, int(layout_nphase or 0))
+        nbytes = workspace_size(self.grid, self.layout_nphase, self.opt)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) & ~255
@@ -296,18 +327,48 @@ class Solver:
         self._c0 = c0
         ctx = ctypes.c_void_p()
         g = (ctypes.c_int * 3)(*self.grid)
-        s = self.lib.hs_create(ctypes.byref(ctx), g, ctypes.byref(m), None if c0 is None else _dp(c0),
-                               ctypes.byref(self.opt), ctypes.c_void_p(self._ws_ptr), ctypes.c_size_t(nbytes),
-                               ctypes.c_void_p(self.stream.cuda_stream))
+        self.workspace_bytes = nbytes
+        s = self.lib.hs_create_sized(ctypes.byref(ctx), g, ctypes.byref(m), None if c0 is None else _dp(c0),
+                                     ctypes.byref(self.opt), self.layout_nphase, ctypes.c_void_p(self._ws_ptr),
+                                     ctypes.c_size_t(nbytes), ctypes.c_void_p(self.stream.cuda_stream))
         _check(self.lib, s)
         self.ctx = ctx
 
-    def solve(self, E, tol=1e-8, max_iter=1000, fields=True):
-        """Returns dict(status, iters, err, sig_eff, eps, sig); eps/sig are torch tensors [6,N3,N2,N1]."""
+    def set_material(self, ids, table, C0=None):
+        """Bind another microstructure of the same grid (hs_set_material): ids [N3][N2][N1] host
+        array, table [nphase][6][6] with nphase <= layout_nphase.  Workspace, launch shapes and
+        captured graphs stay resident."""
+        ids_np = np.ascontiguousarray(ids)
+        if tuple(ids_np.shape) != (self.grid[2], self.grid[1], self.grid[0]) or ids_np.dtype.kind not in "iu":
+            raise ValueError(f"phase ids must be an integer array of shape {(self.grid[2], self.grid[1], self.grid[0])}")
+        kind = HS_IDS_U8 if ids_np.dtype == np.uint8 else HS_IDS_U16
+        if kind == HS_IDS_U16 and ids_np.size and (ids_np.min() < 0 or ids_np.max() > 65535):
+            raise ValueError("phase ids must lie in 0..65535")
+        ids_np = ids_np.astype(np.uint8 if kind == HS_IDS_U8 else np.uint16, copy=False)
+        table = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6))
+        m = hs_material(kind, ctypes.c_void_p(ids_np.ctypes.data), _dp(table), table.shape[0], None)
+        c0 = None if C0 is None else np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(36))
+        _check(self.lib, self.lib.hs_set_material(self.ctx, ctypes.byref(m), None if c0 is None else _dp(c0)),
+               self.ctx)
+        self._ids_keep, self._table, self._c0, self.nphase = ids_np, table, c0, table.shape[0]
+
+    def get_displacement(self):
+        """hs_get_displacement: the FP64 real-space corner displacement [3][N3][N2][N1] (torch tensor)."""
+        torch = self.torch
+        n1, n2, n3 = self.grid
+        out = torch.empty((3, n3, n2, n1), dtype=torch.float64, device=self.workspace.device)
+        _check(self.lib, self.lib.hs_get_displacement(self.ctx, ctypes.c_void_p(out.data_ptr())), self.ctx)
+        return out
+
+    def solve(self, E, tol=1e-8, max_iter=1000, fields=True, out=None):
+        """Returns dict(status, iters, err, sig_eff, eps, sig); eps/sig are torch tensors [6,N3,N2,N1]
+        (``out``: a pair of such tensors to write into instead of new ones)."""
         torch = self.torch
         E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(6))
         eps = sig = None
-        if fields:
+        if fields and out is not None:
+            eps, sig = out
+        elif fields:
             dt = torch.float32 if self.opt.out_f32 else torch.float64
             shp = (6, self.grid[2], self.grid[1], self.grid[0])
             eps = torch.empty(shp, dtype=dt, device=self.workspace.device)
@@ -396,6 +457,103 @@ class Solver:
         if getattr(self, "ctx", None):
             self.lib.hs_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many RVEs and load cases solved in shared launches (thin wrapper over hs_batch_*).
+
+    ``rves``: list of (ids [N3][N2][N1], table [nphase][6][6]) pairs (host arrays); ``item_rve``:
+    the RVE of every item.  The workspace is one PyTorch tensor."""
+
+    def __init__(self, rves, item_rve, precision=HS_FP32_REFINED, device="cuda", stream=None, autotune=False,
+                 **optkw):
+        import torch
+
+        self.lib = load()
+        self.torch = torch
+        self.opt = default_options(precision=precision, **optkw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        nrve = len(rves)
+        self._ids, self._tables = [], []
+        grids = []
+        for ids, table in rves:
+            ids_np = np.ascontiguousarray(ids)
+            if ids_np.ndim != 3 or ids_np.dtype.kind not in "iu":
+                raise TypeError("phase ids must be an integer [N3][N2][N1] array")
+            if ids_np.dtype != np.uint8:
+                if ids_np.size and (ids_np.min() < 0 or ids_np.max() > 65535):
+                    raise ValueError("phase ids must lie in 0..65535")
+                ids_np = ids_np.astype(np.uint16)
+            self._ids.append(ids_np)
+            self._tables.append(np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 6, 6)))
+            n3, n2, n1 = ids_np.shape
+            grids += [n1, n2, n3]
+        self.nitem = len(item_rve)
+        g = (ctypes.c_int * (3 * nrve))(*grids)
+        npn = (ctypes.c_int * nrve)(*[t.shape[0] for t in self._tables])
+        ir = (ctypes.c_int * self.nitem)(*[int(r) for r in item_rve])
+        nbytes = ctypes.c_size_t()
+        _check(self.lib, self.lib.hs_batch_workspace_size(nrve, g, npn, self.nitem, ir, ctypes.byref(self.opt),
+                                                          ctypes.byref(nbytes)))
+        self.workspace_bytes = nbytes.value
+        self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=device)
+        ptr = (self.workspace.data_ptr() + 255) & ~255
+        mats = (hs_material * nrve)()
+        for r in range(nrve):
+            kind = HS_IDS_U8 if self._ids[r].dtype == np.uint8 else HS_IDS_U16
+            mats[r] = hs_material(kind, ctypes.c_void_p(self._ids[r].ctypes.data), _dp(self._tables[r]),
+                                  self._tables[r].shape[0], None)
+        self.stream.wait_stream(torch.cuda.current_stream(device))
+        b = ctypes.c_void_p()
+        s = self.lib.hs_batch_create(ctypes.byref(b), nrve, g, mats, self.nitem, ir, ctypes.byref(self.opt),
+                                     1 if autotune else 0, ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes.value),
+                                     ctypes.c_void_p(self.stream.cuda_stream))
+        if s < 0:
+            raise HSError(s, f"{self.lib.hs_error_string(s).decode()}: {self.lib.hs_batch_last_error(None).decode()}")
+        self.b = b
+
+    def solve(self, E, tol=1e-6, max_iter=1000):
+        """E: (nitem, 6) tensor strains.  Returns dict(status (overall), item_status, iters, err, sig_eff)."""
+        E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(self.nitem, 6))
+        sig = np.zeros((self.nitem, 6))
+        it = np.zeros(self.nitem, dtype=np.int32)
+        err = np.zeros(self.nitem)
+        st = np.zeros(self.nitem, dtype=np.int32)
+        iptr = ctypes.POINTER(ctypes.c_int)
+        s = self.lib.hs_batch_solve(self.b, _dp(E), float(tol), int(max_iter), _dp(sig), it.ctypes.data_as(iptr),
+                                    _dp(err), st.ctypes.data_as(iptr))
+        if s < 0:
+            raise HSError(s, f"{self.lib.hs_error_string(s).decode()}: {self.lib.hs_batch_last_error(self.b).decode()}")
+        return dict(status=s, item_status=st, iters=it, err=err, sig_eff=sig)
+
+    def err_history(self, item, n=1 << 16):
+        out = np.zeros(n)
+        k = ctypes.c_int()
+        _check(self.lib, self.lib.hs_batch_err_history(self.b, int(item), _dp(out), n, ctypes.byref(k)))
+        return out[: k.value]
+
+    def launches(self):
+        n = ctypes.c_longlong()
+        _check(self.lib, self.lib.hs_batch_launches(self.b, ctypes.byref(n)))
+        return n.value
+
+    def classes(self):
+        nc = ctypes.c_int()
+        out = np.zeros(self.nitem, dtype=np.int32)
+        _check(self.lib, self.lib.hs_batch_classes(self.b, ctypes.byref(nc),
+                                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return nc.value, out
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.hs_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

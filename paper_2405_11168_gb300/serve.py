@@ -1,15 +1,22 @@
-"""Continuous-batching RVE solve service on one GPU.
+"""Continuous-batching RVE solve service on one GPU with device-resident solver slots.
 
 Requests (a microstructure, its phase table, 1-6 load cases, a precision and a
 tolerance) are queued as they arrive.  Up to ``slots`` requests run at once,
-each on its own CUDA stream and worker thread; a request is admitted, in
-arrival order, when a slot is free and its device memory (solver workspace from
-``hs_workspace_size`` plus field buffers) fits in the HBM budget next to the
-requests already running.  Solves on different streams overlap on the device
-(the C ABI releases the GIL while it waits).  Every kernel reduction is
-deterministic, so a request's results do not depend on what runs beside it.
+each on its own worker thread.  The device memory is a pool of resident solver
+contexts owned by the HBM budget: a context (workspace, launch shapes, twiddle
+tables, captured iteration graphs, its own CUDA stream, and field buffers when
+asked for) is created for a (grid, precision, phase capacity, fields) key the
+first time a request needs one and stays resident afterwards; a later request of
+the same key binds its microstructure to an idle context with hs_set_material
+instead of allocating anything.  A request is admitted, in arrival order, when a
+worker is free and an idle context of its key exists, or a new one fits in the
+budget next to the resident ones (idle contexts of other keys are released to
+make room).  Solves of different requests run on their contexts' streams and
+overlap on the device (the C ABI releases the GIL while it waits).  Every
+kernel reduction is deterministic, so a request's results do not depend on what
+runs beside it or on which resident context serves it.
 
-A request's launch shapes come from the autotuner's plan cache when
+A context's launch shapes come from the autotuner's plan cache when
 ``autotune=True`` (tuned once per grid and precision, then reused).
 
 The batched form of the 6 unit load cases (the columns of the effective
@@ -26,6 +33,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import hs
+
+# phase capacity of a resident context: materials of up to this many phases share one layout
+LAYOUT_PHASES = 64
 
 
 def unit_loads():
@@ -65,15 +75,43 @@ class Result:
     bytes: int = 0
 
 
-def request_bytes(req: Request) -> int:
-    """Device bytes a request holds while it runs."""
+def layout_phases(nphase: int) -> int:
+    """Phase capacity of the context that serves a material of ``nphase`` phases."""
+    n = LAYOUT_PHASES
+    while n < nphase:
+        n *= 2
+    return min(n, hs.HS_MAX_PHASES)
+
+
+def pool_key(req: Request):
     n3, n2, n1 = req.ids.shape
-    opt = hs.default_options(precision=req.precision)
-    nb = hs.workspace_size((n1, n2, n3), len(req.table), opt) + 256
-    if req.fields:
+    return ((n1, n2, n3), int(req.precision), layout_phases(len(req.table)), bool(req.fields))
+
+
+def key_bytes(key) -> int:
+    """Device bytes a resident context of this key holds (workspace + field buffers)."""
+    (n1, n2, n3), prec, lnp, fields = key
+    opt = hs.default_options(precision=prec)
+    nb = hs.workspace_size((n1, n2, n3), lnp, opt) + 256
+    if fields:
         nb += 2 * 6 * n1 * n2 * n3 * 8
-    nb += n1 * n2 * n3 * 2  # device copy of the ids
     return nb
+
+
+def request_bytes(req: Request) -> int:
+    """Device bytes the context that serves this request holds."""
+    return key_bytes(pool_key(req))
+
+
+@dataclass
+class _Slot:
+    """One resident solver context and what belongs to it."""
+    key: tuple
+    bytes: int
+    stream: object = None
+    solver: object = None
+    fields: tuple = None
+    uses: int = 0
 
 
 class Server:
@@ -86,13 +124,16 @@ class Server:
             dev = torch.device(dev.type, torch.cuda.current_device())
         self.device = dev
         self.budget = int(budget_bytes)
-        self.used = 0
+        self.used = 0               # bytes of every resident context, busy or idle
         self.max_used = 0
         self.running = 0
         self.max_running = 0
+        self.created = 0            # contexts created (the rest of the requests reused one)
+        self.released = 0           # idle contexts released to make room for another key
         self.autotune = autotune
         self._cv = threading.Condition()
         self._pending = collections.deque()
+        self._idle = collections.defaultdict(list)   # key -> idle resident slots
         self._closed = False
         self._workers = []
         for i in range(slots):
@@ -101,14 +142,12 @@ class Server:
             self._workers.append(t)
 
     def request_bytes(self, req: Request) -> int:
-        """Device bytes the request holds while it runs (admission uses this)."""
+        """Device bytes the context that serves the request holds (admission uses this)."""
         return request_bytes(req)
 
     def _start_slot(self):
-        """Per-worker set-up: the device and the worker's own stream."""
-        torch = self.torch
-        torch.cuda.set_device(self.device)
-        return torch.cuda.Stream(self.device)
+        """Per-worker set-up: the worker's device."""
+        self.torch.cuda.set_device(self.device)
 
     def submit(self, req: Request) -> Future:
         need = self.request_bytes(req)
@@ -119,7 +158,7 @@ class Server:
         with self._cv:
             if self._closed:
                 raise RuntimeError("server closed")
-            self._pending.append((req, need, fut))
+            self._pending.append((req, pool_key(req), need, fut))
             self._cv.notify_all()
         return fut
 
@@ -129,42 +168,69 @@ class Server:
             self._cv.notify_all()
         for t in self._workers:
             t.join()
+        with self._cv:
+            for slots in self._idle.values():
+                for sl in slots:
+                    self._free(sl)
+            self._idle.clear()
 
-    # admission: the head of the queue runs when its bytes fit next to the running requests
+    def _free(self, sl: _Slot):
+        if sl.solver is not None:
+            sl.solver.close()
+        sl.solver = sl.fields = None
+        self.used -= sl.bytes
+
+    # admission: the head of the queue runs when an idle context of its key is resident, or a new
+    # one fits next to the resident contexts once idle contexts of other keys are released
     def _take(self):
         with self._cv:
             while True:
                 if self._pending:
-                    req, need, fut = self._pending[0]
-                    if self.used + need <= self.budget:
+                    req, key, need, fut = self._pending[0]
+                    if self._idle[key]:
+                        sl = self._idle[key].pop()
+                    else:
+                        others = [s for k, lst in self._idle.items() if k != key for s in lst]
+                        while self.used + need > self.budget and others:
+                            victim = others.pop(0)
+                            self._idle[victim.key].remove(victim)
+                            self._free(victim)
+                            self.released += 1
+                        sl = None
+                        if self.used + need <= self.budget:
+                            sl = _Slot(key=key, bytes=need)
+                            self.used += need
+                            self.created += 1
+                    if sl is not None:
                         self._pending.popleft()
-                        self.used += need
                         self.running += 1
                         self.max_used = max(self.max_used, self.used)
                         self.max_running = max(self.max_running, self.running)
-                        return req, need, fut
+                        return req, sl, fut
                 elif self._closed:
                     return None
                 self._cv.wait()
 
-    def _release(self, need):
+    def _release(self, sl: _Slot, ok: bool):
         with self._cv:
-            self.used -= need
             self.running -= 1
+            if ok and sl.solver is not None:
+                self._idle[sl.key].append(sl)       # stays resident for the next request of its key
+            else:
+                self._free(sl)
             self._cv.notify_all()
 
     def _fail_pending(self, exc):
         with self._cv:
             while self._pending:
-                _, _, fut = self._pending.popleft()
+                _, _, _, fut = self._pending.popleft()
                 fut.set_exception(exc)
             self._closed = True
             self._cv.notify_all()
 
     def _worker(self):
-        torch = self.torch
         try:
-            stream = self._start_slot()
+            self._start_slot()
         except BaseException as e:  # noqa: BLE001 - a slot that cannot start fails the queue, not silently
             self._fail_pending(e)
             return
@@ -172,49 +238,60 @@ class Server:
             item = self._take()
             if item is None:
                 return
-            req, need, fut = item
+            req, sl, fut = item
             t_start = time.perf_counter()
+            ok = False
             try:
-                if stream is not None:
-                    with torch.cuda.stream(stream):
-                        res = self._run(req, stream)
-                    stream.synchronize()
-                else:
-                    res = self._run(req, stream)
+                res = self._run(req, sl)
                 res.queued_s = t_start - req.arrival
                 res.latency_s = time.perf_counter() - req.arrival
-                res.bytes = need
+                res.bytes = sl.bytes
+                ok = True
                 fut.set_result(res)
             except BaseException as e:  # noqa: BLE001 - report any failure through the future
                 fut.set_exception(e)
             finally:
-                self._release(need)
+                self._release(sl, ok)
 
-    def _run(self, req: Request, stream) -> Result:
+    def _bind(self, req: Request, sl: _Slot):
+        """The slot's context bound to the request's microstructure (created on first use)."""
         torch = self.torch
-        ids = torch.from_numpy(np.ascontiguousarray(req.ids)).to(self.device)
+        if sl.solver is not None:
+            sl.solver.set_material(req.ids, req.table)
+            return
+        sl.stream = torch.cuda.Stream(self.device)
         kw = {}
         if self.autotune:
-            opts, _ = hs.autotune(ids, req.table, precision=req.precision, device=self.device, stream=stream)
+            opts, _ = hs.autotune(torch.from_numpy(np.ascontiguousarray(req.ids)).to(self.device), req.table,
+                                  precision=req.precision, device=self.device, stream=sl.stream)
             kw = {k: opts[k] for k in ("ytile", "zchunk", "col_tile")}
-        s = hs.Solver(ids, req.table, precision=req.precision, device=self.device, stream=stream, **kw)
-        try:
-            sig_eff, iters, errs, status = [], [], [], []
-            out = None
-            for k, E in enumerate(req.loads):
-                last = k == len(req.loads) - 1
-                out = s.solve(E, tol=req.tol, max_iter=req.max_iter, fields=req.fields and last)
-                sig_eff.append(out["sig_eff"])
-                iters.append(out["iters"])
-                errs.append(out["err"])
-                status.append(out["status"])
-            res = Result(tag=req.tag, sig_eff=np.array(sig_eff), iters=iters, errs=errs, status=status)
-            if req.fields:
-                res.eps = out["eps"].cpu().numpy()
-                res.sig = out["sig"].cpu().numpy()
-            return res
-        finally:
-            s.close()
+        sl.solver = hs.Solver(req.ids, req.table, precision=req.precision, device=self.device, stream=sl.stream,
+                              layout_nphase=sl.key[2], **kw)
+        if req.fields:
+            n3, n2, n1 = req.ids.shape
+            sl.fields = (torch.empty((6, n3, n2, n1), dtype=torch.float64, device=self.device),
+                         torch.empty((6, n3, n2, n1), dtype=torch.float64, device=self.device))
+
+    def _run(self, req: Request, sl: _Slot) -> Result:
+        self._bind(req, sl)
+        sl.uses += 1
+        s = sl.solver
+        sig_eff, iters, errs, status = [], [], [], []
+        out = None
+        for k, E in enumerate(req.loads):
+            last = k == len(req.loads) - 1
+            out = s.solve(E, tol=req.tol, max_iter=req.max_iter, fields=req.fields and last,
+                          out=sl.fields if (req.fields and last) else None)
+            sig_eff.append(out["sig_eff"])
+            iters.append(out["iters"])
+            errs.append(out["err"])
+            status.append(out["status"])
+        res = Result(tag=req.tag, sig_eff=np.array(sig_eff), iters=iters, errs=errs, status=status)
+        if req.fields:
+            sl.stream.synchronize()
+            res.eps = out["eps"].cpu().numpy()
+            res.sig = out["sig"].cpu().numpy()
+        return res
 
 
 def run_stream(server: Server, requests, rate_hz: float, seed: int = 0):
@@ -299,6 +376,7 @@ def main(argv=None):
             "solves": solves, "converged": conv, "wall_s": wall, "precision": a.precision, "tol": a.tol,
             "max_iter": a.max_iter, "sizes": sizes, "rate_hz": a.rate, "slots": a.slots,
             "budget_gb": a.budget_gb, "max_running": srv.max_running, "max_used_gb": srv.max_used / 2**30,
+            "contexts_created": srv.created, "contexts_released": srv.released,
             "evaluations": int(sum(sum(r.iters) for r in res)), **latency_stats(res)}
     print(json.dumps(line), flush=True)
     return 0

@@ -1,9 +1,11 @@
-"""The serving runtime: the same results alone and in the mix, admission by HBM budget,
+"""The serving runtime: the same results alone and in the mix, both equal to the oracle within
+each request's tolerance; resident contexts reused across requests; admission by HBM budget;
 and the autotuner's plan cache."""
 import numpy as np
 import pytest
 
 import synth
+from oracle import tetra as T
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -20,17 +22,32 @@ def hs():
     return _hs
 
 
+# (grid, contrast, precision, loads, tol): the FP32 path stops at 1e-5 (its rounding floor is a
+# few 1e-6); refined requests include voids and the rigid surrogate 1e6
+SPECS = [((16, 16, 16), 5.0, 2, 6, 1e-8), ((24, 24, 24), 0.01, 1, 2, 1e-5), ((16, 24, 12), 50.0, 0, 3, 1e-8),
+         ((32, 32, 32), 0.0, 2, 1, 1e-8), ((24, 18, 12), 1e6, 2, 2, 1e-6)]
+
+
 def _requests(hs, serve):
     reqs = []
-    specs = [((16, 16, 16), 5.0, hs.HS_FP32_REFINED, 6), ((24, 24, 24), 0.01, hs.HS_FP32, 2),
-             ((16, 24, 12), 50.0, hs.HS_FP64, 3), ((32, 32, 32), 0.0, hs.HS_FP32_REFINED, 1),
-             ((24, 18, 12), 1e6, hs.HS_FP32_REFINED, 2)]
-    for i, (grid, contrast, prec, nl) in enumerate(specs):
+    for i, (grid, contrast, prec, nl, tol) in enumerate(SPECS):
         ids = synth.centred_sphere(grid, volume_fraction=0.2)
         table = synth.two_phase_table(1.0, 0.3, contrast, 0.3)
-        reqs.append(serve.Request(ids=ids, table=table, loads=serve.unit_loads()[:nl], precision=prec, tol=1e-6,
-                                  max_iter=400, fields=True, tag=i))
+        reqs.append(serve.Request(ids=ids, table=table, loads=serve.unit_loads()[:nl], precision=prec, tol=tol,
+                                  max_iter=5000, fields=True, tag=i))
     return reqs
+
+
+def _oracle(req):
+    """Converged <sigma> of every load and the fields of the last one, FP64 oracle (tol 1e-10; the
+    rigid surrogate's FP64 floor is near 1e-9, so 1e-9 there)."""
+    lam0 = T.c0_alpha_rule(req.table)
+    tol = 1e-9 if req.table[1, 0, 0] > 1e5 else 1e-10
+    sig, last = [], None
+    for E in req.loads:
+        last = T.solve_alg1(req.ids, req.table, lam0, T.strain_tensor_from_voigt(E), tol=tol, max_iter=5000)
+        sig.append(T.voigt_from_tensor(last.sig_mean))
+    return np.array(sig), T.voigt_from_tensor(last.eps), T.voigt_from_tensor(last.sig)
 
 
 def test_same_alone_and_in_the_mix(hs):
@@ -57,6 +74,45 @@ def test_same_alone_and_in_the_mix(hs):
         np.testing.assert_array_equal(a.sig_eff, b.sig_eff)
         np.testing.assert_array_equal(a.eps, b.eps)
         np.testing.assert_array_equal(a.sig, b.sig)
+    # every served result against the oracle, within its request's tolerance
+    for req in _requests(hs, serve):
+        res = alone[req.tag]
+        assert all(st == hs.HS_OK for st in res.status), (req.tag, res.status, res.errs)
+        assert all(e < req.tol for e in res.errs)
+        sig_ref, e_ref, s_ref = _oracle(req)
+        bound = {hs.HS_FP64: 1e-6, hs.HS_FP32: 1e-4, hs.HS_FP32_REFINED: 2e-5}[req.precision]
+        np.testing.assert_allclose(res.sig_eff, sig_ref, rtol=0, atol=bound * np.abs(sig_ref).max())
+        assert np.linalg.norm(res.sig - s_ref) <= bound * np.linalg.norm(s_ref), req.tag
+        assert np.linalg.norm(res.eps - e_ref) <= bound * np.linalg.norm(e_ref), req.tag
+
+
+def test_resident_contexts_are_reused(hs):
+    """Six requests of one grid and precision through one worker: one context is created and the
+    other five bind their microstructures to it (hs_set_material); every result equals that of a
+    fresh solver."""
+    from paper_2405_11168_gb300 import serve
+
+    grid = (24, 24, 24)
+    reqs = []
+    for i, contrast in enumerate([3.0, 0.1, 0.0, 40.0, 0.5, 8.0]):
+        ids = synth.centred_sphere(grid, volume_fraction=0.1 + 0.03 * i)
+        reqs.append(serve.Request(ids=ids, table=synth.two_phase_table(1.0, 0.3, contrast, 0.3),
+                                  loads=serve.unit_loads()[:2], precision=hs.HS_FP32_REFINED, tol=1e-7,
+                                  max_iter=3000, fields=True, tag=i))
+    srv = serve.Server(budget_bytes=4 << 30, slots=1)
+    try:
+        res = [srv.submit(r).result(timeout=300) for r in reqs]
+    finally:
+        srv.close()
+    assert srv.created == 1
+    for r, got in zip(reqs, res):
+        s = hs.Solver(r.ids, r.table, precision=r.precision)
+        for k, E in enumerate(r.loads):
+            ref = s.solve(E, tol=r.tol, max_iter=r.max_iter, fields=(k == len(r.loads) - 1))
+            assert ref["iters"] == got.iters[k] and ref["err"] == got.errs[k]
+            np.testing.assert_array_equal(ref["sig_eff"], got.sig_eff[k])
+        np.testing.assert_array_equal(ref["eps"].cpu().numpy(), got.eps)
+        s.close()
 
 
 def test_admission_respects_the_budget(hs):
