@@ -102,11 +102,14 @@ typedef struct {
   int use_graphs;       /* 1 (default): after its first chunk, a solve replays its iteration chunks
                            (check_every iterations) as one captured CUDA graph; 0: plain launches.
                            Chunks that profiling times (hs_profile_enable) run as plain launches. */
+  int col_state;        /* z pass + Green update: 0 = automatic, 1 = state read point by point (L2
+                           prefetch), 2 = state tile copied to shared memory during the forward z
+                           transform (twice the tile's shared memory); results do not change */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
  * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0, col_tile 0, col_threads 0,
- * use_graphs 1. */
+ * use_graphs 1, col_state 0. */
 hs_status hs_default_options(hs_options* opt);
 
 /* Autotuner with a process-wide plan cache (no counterpart in the paper: it picks launch

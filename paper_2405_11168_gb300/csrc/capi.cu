@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -185,8 +186,19 @@ bool cholesky_pd(const double* A) {
 }
 
 struct Layout {
-  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, c0, u64, rsrc, total;
+  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, c0, side, rpart, u64, rsrc,
+      total;
 };
+
+// Row groups (one voxel row each) per block of the FP32 column-pair pass: up to
+// 8 groups of round-up(N1/2, 32) threads within 512 threads, dividing N2.
+int xp_groups(int n1, int n2) {
+  const int nt = ((n1 / 2 + 31) / 32) * 32;
+  int rg = std::min(8, 512 / nt);
+  while (rg > 1 && n2 % rg != 0) rg /= 2;
+  return rg;
+}
+constexpr int kMaxRowBlocks = 4096;  // per-block |F|^2 sums of the forward x pass
 
 }  // namespace
 
@@ -209,6 +221,13 @@ struct hs_ctx {
   int batch_n = 1;
   size_t batch_stride = 0;
   int layout_np = 1;        // phase count the workspace layout was sized for (>= nphase)
+  // FP32 iterations (xfuse = 0): the column-pair real-space pass k_xpair
+  bool xp = false;
+  int xp_rg = 0, xp_nthr = 0, xp_zc = 0;
+  dim3 grid_xp;
+  size_t smem_xp = 0, smem_xp_src = 0;
+  float* side = nullptr;
+  double* rpart = nullptr;
   bool unbound = false;     // a failed hs_set_material left the workspace without a valid material
   char* ws;
   size_t ws_bytes;
@@ -248,6 +267,7 @@ struct hs_ctx {
   int nthr_row, nblk_row[2];  // [ROW_C2R], [ROW_R2C]
   size_t smem_row[2];
   size_t smem_y, smem_z;
+  bool zstate_smem = false;  // the z pass copies the state tile to shared memory
   dim3 grid_y, grid_z;
   bool warm;
   int cur;
@@ -515,6 +535,9 @@ Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
   L.sig0f = off; off += align256((size_t)nphase * 6 * 4);
   L.sig0d = off; off += align256((size_t)nphase * 6 * 8);
   L.c0 = off; off += align256(32);  // isotropic reference medium (lambda0 + mu0, mu0): 2 double, then 2 float
+  // FP32 iterations: the column-pair pass's partial rows at block boundaries, the row pass's sums
+  L.side = off; off += f64 ? 0 : align256((size_t)3 * n3 * (n2 / xp_groups(n1, n2)) * n1 * 4);
+  L.rpart = off; off += f64 ? 0 : align256((size_t)kMaxRowBlocks * 8);
   L.u64 = off;
   L.rsrc = off;
   if (prec == HS_FP32_REFINED) {
@@ -572,6 +595,7 @@ template <typename T> void fill_col(hs_ctx* c, hs::ColArgs<T>& a, void* buf, int
   a.st = c->st;
   a.skip_if_done = 1;
   a.zstride = c->batch_stride;
+  a.state_smem = (axis == 2 && c->zstate_smem) ? 1 : 0;
 }
 
 template <typename T> hs_status launch_force(hs_ctx* c, const double E[6], int in, const float* src) {
@@ -610,6 +634,19 @@ template <typename T> hs_status launch_rows(hs_ctx* c, int mode, double* acc64, 
   a.st = c->st;
   a.skip_if_done = skip ? 1 : 0;
   a.zstride = c->batch_stride;
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->xp && mode == hs::ROW_R2C) {
+      // complete the rows the column-pair pass left partial, sum |F|^2, take the stopping test
+      a.side = c->side;
+      a.srows = c->xp_rg;
+      a.n2 = c->n2;
+      a.n3 = c->n3;
+      a.spart = c->partials;
+      a.nspart = (int)(c->grid_xp.x * c->grid_xp.y);
+      a.rpart = c->rpart;
+      a.hist = c->hist;
+    }
+  }
   cudaError_t e;
   {
     LaunchScope ls(c, acc64 ? HS_K_OTHER : (mode == hs::ROW_C2R ? HS_K_XINV : HS_K_XFWD));
@@ -645,6 +682,43 @@ template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], con
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(real)");
   return HS_OK;
+}
+
+// the real-space pass of one iteration: k_xpair for FP32, k_march for FP64
+template <typename T> hs_status launch_xpass(hs_ctx* c, const double E[6], const float* src) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->xp) {
+      hs::XpArgs a;
+      memset(&a, 0, sizeof(a));
+      a.ureal = (const float*)c->B[1];
+      a.ids = c->ids;
+      a.mat = (const float*)c->matk;
+      a.fout = (float*)c->F;
+      a.side = c->side;
+      a.src = src;
+      a.partials = c->partials;
+      a.st = c->st;
+      // the correction equation K du = -r is linear: no eigenstrain, macro strain 0
+      a.Edev = src != nullptr ? nullptr : &c->st->E[0];
+      a.sig0 = (src != nullptr || !c->has_eigen) ? nullptr : c->sig0f;
+      for (int i = 0; i < 6; ++i) a.E[i] = src != nullptr ? 0.f : (float)E[i];
+      a.n1 = c->n1;
+      a.n2 = c->n2;
+      a.n3 = c->n3;
+      a.zc = c->xp_zc;
+      a.skip_if_done = 1;
+      a.zstride = c->batch_stride;
+      cudaError_t e;
+      {
+        LaunchScope ls(c, src != nullptr ? HS_K_XPASS_SRC : HS_K_XPASS);
+        e = hs::launch_xpair(a, c->iso, 1, zg(c, c->grid_xp), c->xp_nthr, src != nullptr ? c->smem_xp_src : c->smem_xp,
+                             c->stream);
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "k_xpair");
+      return HS_OK;
+    }
+  }
+  return launch_stencil<T>(c, E, src, hs::MODE_FORCE, nullptr, nullptr);
 }
 
 template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
@@ -783,7 +857,7 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
         cur ^= 1;
       } else {
         hs_status s = launch_rows<T>(c, hs::ROW_C2R, nullptr, true);
-        if (s == HS_OK) s = launch_stencil<T>(c, E, src, hs::MODE_FORCE, nullptr, nullptr);
+        if (s == HS_OK) s = launch_xpass<T>(c, E, src);
         if (s == HS_OK) s = launch_rows<T>(c, hs::ROW_R2C, nullptr, true);
         if (s == HS_OK) s = launch_cols<T>(c, 0);
         if (s != HS_OK) {
@@ -852,7 +926,9 @@ hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, vo
     if (c->xfuse) {
       s = launch_fields<T>(c, E, last_in, eps, sig);
     } else {
-      s = launch_rows<T>(c, hs::ROW_C2R, nullptr, false);
+      // B[1] still holds the real displacement of the last evaluation when the column-pair pass
+      // ran it (its stopping test, in the forward x pass, let that pass overwrite B[0])
+      s = c->xp ? HS_OK : launch_rows<T>(c, hs::ROW_C2R, nullptr, false);
       if (s == HS_OK) s = launch_stencil<T>(c, E, nullptr, hs::MODE_FIELDS, eps, sig);
     }
     if (s != HS_OK) return s;
@@ -1066,6 +1142,7 @@ hs_status hs_default_options(hs_options* opt) {
   opt->col_tile = 0;
   opt->col_threads = 0;
   opt->use_graphs = 1;
+  opt->col_state = 0;
   return HS_OK;
 }
 
@@ -1110,7 +1187,7 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0 ||
       !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
       (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0 ||
-      (o.use_graphs != 0 && o.use_graphs != 1))
+      (o.use_graphs != 0 && o.use_graphs != 1) || o.col_state < 0 || o.col_state > 2)
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > HS_MAX_PHASES)
@@ -1223,6 +1300,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
   c->macro = (double*)(c->ws + c->lay.macro);
   c->sig0f = (float*)(c->ws + c->lay.sig0f);
   c->sig0d = (double*)(c->ws + c->lay.sig0d);
+  c->side = c->f64 ? nullptr : (float*)(c->ws + c->lay.side);
+  c->rpart = c->f64 ? nullptr : (double*)(c->ws + c->lay.rpart);
   c->u64 = (o.precision == HS_FP32_REFINED) ? (double*)(c->ws + c->lay.u64) : nullptr;
   c->rsrc = (o.precision == HS_FP32_REFINED) ? (float*)(c->ws + c->lay.rsrc) : nullptr;
   c->warm = false;
@@ -1295,6 +1374,25 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
     delete c;
     return st;
   }
+  // FP32 iterations: the column-pair pass, row groups of round-up(N1/2, 32) threads
+  if (!c->f64 && !c->xfuse) {
+    c->xp = true;
+    c->xp_rg = xp_groups(c->n1, c->n2);
+    c->xp_nthr = c->xp_rg * (((c->n1 / 2 + 31) / 32) * 32);
+    const int yt = c->n2 / c->xp_rg;
+    int nz = std::max(1, std::min(c->n3, (kTargetBlocks + yt - 1) / yt));
+    c->xp_zc = (c->n3 + nz - 1) / nz;
+    if (o.zchunk > 0) c->xp_zc = std::min(o.zchunk, c->n3);
+    nz = (c->n3 + c->xp_zc - 1) / c->xp_zc;
+    c->grid_xp = dim3(yt, nz);
+    const int nt = ((c->n1 / 2 + 31) / 32) * 32;
+    c->smem_xp = hs::xp_layout(c->n1, nt, c->xp_rg, 1, false).total;
+    c->smem_xp_src = hs::xp_layout(c->n1, nt, c->xp_rg, 1, true).total;
+    if ((size_t)yt * nz > (size_t)((c->n2 / 2) * c->n3) || c->smem_xp_src > (size_t)smem_optin) {
+      delete c;
+      return fail(nullptr, HS_ERR_UNSUPPORTED_SIZE, "grid too large for the column-pair pass");
+    }
+  }
   // real-space pass: an automatic row tile is halved while its plane ring does not fit
   // (FP64 rows of 512 need 2 rows per block)
   if (o.ytile == 0 && !c->xfuse) {
@@ -1323,6 +1421,11 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
     nz = (c->n3 + c->zc64 - 1) / c->zc64;
     c->grid_m64 = dim3(yt, nz);
   }
+  // z pass: the state tile in shared memory beside the force tile when asked for (col_state = 2)
+  if (o.col_state == 2 && 2 * c->smem_z <= (size_t)smem_optin) {
+    c->zstate_smem = true;
+    c->smem_z *= 2;
+  }
   const size_t need = std::max({c->xfuse ? march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, false, true)
                                           : march_smem(c->n1, c->ty, c->f64, hs::MODE_FORCE, true, true),
                                 c->smem_row[0], c->smem_row[1],
@@ -1343,7 +1446,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       int per_sm = 0;
       e = c->f64 ? hs::row_blocks_per_sm<double>(m, c->n1, c->nthr_row, c->smem_row[m], &per_sm)
                  : hs::row_blocks_per_sm<float>(m, c->n1, c->nthr_row, c->smem_row[m], &per_sm);
-      c->nblk_row[m] = (int)std::min<size_t>(nbatch, (size_t)std::max(1, per_sm) * std::max(1, nsm));
+      c->nblk_row[m] = (int)std::min<size_t>({nbatch, (size_t)std::max(1, per_sm) * std::max(1, nsm),
+                                              (size_t)kMaxRowBlocks});
     }
     if (e != cudaSuccess) {
       hs_status st = cuda_fail(nullptr, e, "row pass occupancy");
@@ -2093,7 +2197,7 @@ template <typename T> hs_status batch_iterate(hs_batch* b, bool with_src) {
   auto one_chunk = [&](hs_ctx* L) -> hs_status {
     for (int i = 0; i < chunk; ++i) {
       hs_status s = launch_rows<T>(L, hs::ROW_C2R, nullptr, true);
-      if (s == HS_OK) s = launch_stencil<T>(L, zeroE, with_src ? L->rsrc : nullptr, hs::MODE_FORCE, nullptr, nullptr);
+      if (s == HS_OK) s = launch_xpass<T>(L, zeroE, with_src ? L->rsrc : nullptr);
       if (s == HS_OK) s = launch_rows<T>(L, hs::ROW_R2C, nullptr, true);
       if (s == HS_OK) s = launch_cols<T>(L, 0);
       if (s != HS_OK) return s;

@@ -42,6 +42,8 @@ template <typename T> struct ColArgs {
   const DevStatus* st;
   int skip_if_done;
   size_t zstride;    // batched launches: bytes between the workspaces of consecutive items
+  int state_smem;    // COL_Z_GREEN: 1 = the state tile is copied to shared memory beside the force
+                     // tile (its copy overlaps the forward transform); 0 = read point by point
 };
 
 template <typename T> __device__ __forceinline__ ColArgs<T> col_item_args(const ColArgs<T>& a) {
@@ -128,9 +130,9 @@ __device__ __forceinline__ void green_apply(const ColArgs<T>& a, T c0a, T c0b, b
 // transformed force F(q) of the tile; the state u(q) is read from and written
 // to a.S, and the new u(q) replaces F(q) in sm for the inverse transform.
 template <typename T, int CT>
-__device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T>::type* sm, size_t base,
-                                          size_t rstride, size_t cstride, int x0, int outer, int ncol, int L,
-                                          int tid, int nthr) {
+__device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T>::type* sm,
+                                          const typename cplx_t<T>::type* ss, size_t base, size_t rstride,
+                                          size_t cstride, int x0, int outer, int ncol, int L, int tid, int nthr) {
   const bool c0iso = a.c0iso || a.c0dev != nullptr;
   const T c0a = a.c0dev != nullptr ? a.c0dev[0] : a.c0a;
   const T c0b = a.c0dev != nullptr ? a.c0dev[1] : a.c0b;
@@ -144,9 +146,14 @@ __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T
       const int i = i0 + u * nthr;
       const int z = i / CT, col = i - z * CT;
       if (i < L * CT && col < ncol) {
-        const size_t g = base + z * rstride + col;
+        if (ss != nullptr) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) U[u][c] = a.S[c * cstride + g];
+          for (int c = 0; c < 3; ++c) U[u][c] = ss[z * W + c * CT + col];
+        } else {
+          const size_t g = base + z * rstride + col;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) U[u][c] = a.S[c * cstride + g];
+        }
       }
     }
 #pragma unroll
@@ -209,15 +216,30 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
     }
   }
   cp_async_commit();
+  C* ss = nullptr;  // state tile in shared memory (COL_Z_GREEN with state_smem)
   if (MODE == COL_Z_GREEN) {
-    // the Green step reads the state tile after the forward transform: start
-    // moving it into L2 now (one prefetch per 64-byte row segment)
-    for (int i = tid; i < L * 3; i += nthr) {
-      const int e = i / 3, c = i - 3 * e;
-      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
+    if (a.state_smem) {
+      // the state tile follows the force tile; its copy (a second group) overlaps the forward
+      // transform, which waits for the first group only
+      ss = sm + (size_t)L * W;
+      for (int i = tid; i < L * 3 * CPR; i += nthr) {
+        const int e = i / (3 * CPR), rem = i - e * (3 * CPR), c = rem / CPR, col = (rem - c * CPR) * EPC;
+        if (col < ccols) cp_async16(ss + e * W + c * CT + col, a.S + c * cstride + base + e * rstride + col);
+      }
+      cp_async_commit();
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      // the Green step reads the state tile after the forward transform: start
+      // moving it into L2 now (one prefetch per 64-byte row segment)
+      for (int i = tid; i < L * 3; i += nthr) {
+        const int e = i / 3, c = i - 3 * e;
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
+      }
+      cp_async_wait_all();
     }
+  } else {
+    cp_async_wait_all();
   }
-  cp_async_wait_all();
   __syncthreads();
   if constexpr (LF > 0) {
     // compile-time plan; the last stage writes straight to global memory
@@ -230,7 +252,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
     io.ncol = ncol;
     if (MODE == COL_Z_GREEN) {
       fft_col_fixed<LF, W, CT, false, false, false>(sm, io, tw, tid, nthr);
-      col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+      if (ss != nullptr) {
+        cp_async_wait_all();
+        __syncthreads();
+      }
+      col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
       __syncthreads();
       fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, nthr);
     } else {
@@ -245,7 +271,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
     fft_smem<false, true, EXT>(sm, 1, W, -1, W, plan.L, plan.nstage, plan.packed, tw, tid, nthr);
   }
   if (MODE == COL_Z_GREEN) {
-    col_green<T, CT>(a, sm, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+    if (ss != nullptr) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
     __syncthreads();
     fft_smem<true, true, EXT>(sm, 1, W, -1, W, plan.L, plan.nstage, plan.packed, tw, tid, nthr);
   }

@@ -93,35 +93,103 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Evaluation of the stopping test from the sums of one residual evaluation
+// (Eqs. L2-norm, tolerance): sums[0..5] = sum over voxels of sigma^T1 + sigma^T2,
+// sums[6] = sum over corners of |F|^2.  Updates the status (error, history,
+// done flag, applied-stress strain update) and clears the arrival counter.
+// One thread calls it.
+__device__ inline void finalize_eval(DevStatus* st, double* hist, const double* sums) {
+  const double n = st->nvox;
+  double sm[6], nrm2 = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    sm[i] = 0.5 * sums[i] / n;
+    nrm2 += (i < 3 ? 1.0 : 2.0) * sm[i] * sm[i];
+    st->sig_mean[i] = sm[i];
+  }
+  const double l2 = sqrt(sums[6] / n);
+  const double nrm = sqrt(nrm2);
+  const double den = st->denom > 0 ? st->denom : nrm;
+  double err;
+  if (den > 0) err = l2 / den;
+  else err = (l2 == 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
+  st->l2 = l2;
+  st->sig_norm = nrm;
+  st->err = err;
+  const int k = st->evals;
+  if (k < st->hist_cap) hist[k] = err;
+  st->evals = k + 1;
+  if (!(err == err) || err > 1e300) {
+    st->done = DONE_DIVERGED;
+  } else {
+    if (k == 0 || err < st->err_min) st->err_min = err;
+    if (k == 0) st->err_first = err;
+    if (err < st->tol || (st->rel_tol > 0 && err <= st->rel_tol * st->err_first)) st->done = DONE_CONVERGED;
+    else if (err > 1e6 * st->err_min && k > 10) st->done = DONE_DIVERGED;
+    else if (k + 1 >= st->max_iter) st->done = DONE_MAXITER;
+  }
+  if (st->macro != nullptr && st->done == DONE_RUNNING) {
+    // E <- (lambda0)^-1 : {sigma^a + (lambda0 - <lambda>) : E - <lambda : deps> + <lambda : eps0>}
+    //    = E + (lambda0)^-1 : (sigma^a - <sigma>)   (the same quantity, regrouped)
+    const double* Sa = st->macro;
+    const double* S0 = st->macro + 6;
+    double d[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = Sa[i] - sm[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double acc = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc += S0[i * 6 + j] * d[j];
+      st->E[i] += acc;
+    }
+  }
+  st->counter = 0;
+}
+
+// Block-sum NV doubles (fixed order) into dst[0 .. NV-1].  scratch: >= 32 * NV
+// doubles of shared memory.  Every thread of the block must call it.
+template <int NV>
+__device__ inline void block_sum(const double (&acc)[NV], double* dst, double* scratch) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = warp_sum(acc[v]);
+    if (lane == 0) scratch[warp * NV + v] = s;
+  }
+  __syncthreads();
+  if (tid < NV) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += scratch[w * NV + tid];
+    dst[tid] = s;
+  }
+}
+
+// After every block has written its partials: true in the one block that
+// arrives last (all partials of the launch visible to it).
+__device__ inline bool last_block_arrived(DevStatus* st, unsigned int nblk) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(&st->counter, 1u);
+    am_last = (prev == nblk - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
 // Block-sum NRED doubles (fixed order) and publish them as this block's
 // partials; the last block to arrive reduces all partials in index order and
-// updates the status.  scratch: >= 32 * NRED doubles of shared memory.
+// evaluates the stopping test.  scratch: >= 32 * NRED doubles of shared memory.
 __device__ inline void reduce_and_finalize(const double (&acc)[NRED], double* partials, DevStatus* st,
                                            double* hist, double* scratch) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
   const int nblk = gridDim.x * gridDim.y;
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  __shared__ bool am_last;
-#pragma unroll
-  for (int v = 0; v < NRED; ++v) {
-    double s = warp_sum(acc[v]);
-    if (lane == 0) scratch[warp * NRED + v] = s;
-  }
-  __syncthreads();
-  if (tid < NRED) {
-    double s = 0;
-    for (int w = 0; w < nw; ++w) s += scratch[w * NRED + tid];
-    partials[(size_t)bid * NRED + tid] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    unsigned int prev = atomicAdd(&st->counter, 1u);
-    am_last = (prev == (unsigned int)(nblk - 1));
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
+  block_sum<NRED>(acc, partials + (size_t)bid * NRED, scratch);
+  if (!last_block_arrived(st, (unsigned)nblk)) return;
   // deterministic: value v by warp (v mod nw), lanes stride over blocks
   for (int v = warp; v < NRED; v += nw) {
     double s = 0;
@@ -130,54 +198,7 @@ __device__ inline void reduce_and_finalize(const double (&acc)[NRED], double* pa
     if (lane == 0) scratch[v] = s;
   }
   __syncthreads();
-  if (tid == 0) {
-    const double n = st->nvox;
-    double sm[6], nrm2 = 0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      sm[i] = 0.5 * scratch[i] / n;
-      nrm2 += (i < 3 ? 1.0 : 2.0) * sm[i] * sm[i];
-      st->sig_mean[i] = sm[i];
-    }
-    const double l2 = sqrt(scratch[6] / n);
-    const double nrm = sqrt(nrm2);
-    const double den = st->denom > 0 ? st->denom : nrm;
-    double err;
-    if (den > 0) err = l2 / den;
-    else err = (l2 == 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
-    st->l2 = l2;
-    st->sig_norm = nrm;
-    st->err = err;
-    const int k = st->evals;
-    if (k < st->hist_cap) hist[k] = err;
-    st->evals = k + 1;
-    if (!(err == err) || err > 1e300) {
-      st->done = DONE_DIVERGED;
-    } else {
-      if (k == 0 || err < st->err_min) st->err_min = err;
-      if (k == 0) st->err_first = err;
-      if (err < st->tol || (st->rel_tol > 0 && err <= st->rel_tol * st->err_first)) st->done = DONE_CONVERGED;
-      else if (err > 1e6 * st->err_min && k > 10) st->done = DONE_DIVERGED;
-      else if (k + 1 >= st->max_iter) st->done = DONE_MAXITER;
-    }
-    if (st->macro != nullptr && st->done == DONE_RUNNING) {
-      // E <- (lambda0)^-1 : {sigma^a + (lambda0 - <lambda>) : E - <lambda : deps> + <lambda : eps0>}
-      //    = E + (lambda0)^-1 : (sigma^a - <sigma>)   (the same quantity, regrouped)
-      const double* Sa = st->macro;
-      const double* S0 = st->macro + 6;
-      double d[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) d[i] = Sa[i] - sm[i];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        double acc = 0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) acc += S0[i * 6 + j] * d[j];
-        st->E[i] += acc;
-      }
-    }
-    st->counter = 0;
-  }
+  if (tid == 0) finalize_eval(st, hist, scratch);
 }
 
 }  // namespace hs
