@@ -652,7 +652,10 @@ template <typename T> hs_status launch_rows(hs_ctx* c, int mode, double* acc64, 
     LaunchScope ls(c, acc64 ? HS_K_OTHER : (mode == hs::ROW_C2R ? HS_K_XINV : HS_K_XFWD));
     e = hs::launch_row<T>(a, mode, zg(c, dim3(c->nblk_row[mode])), c->nthr_row, c->smem_row[mode], c->stream);
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "k_row");
+  if (e != cudaSuccess)
+    return cuda_fail(c, e, (std::string("k_row(") + (mode == hs::ROW_C2R ? "C2R" : "R2C") + ", blocks " +
+                            std::to_string(c->nblk_row[mode]) + ", smem " + std::to_string(c->smem_row[mode]) + ")")
+                               .c_str());
   return HS_OK;
 }
 
@@ -1846,14 +1849,17 @@ hs_status hs_autotune(const int grid[3], const hs_material* m_in, const hs_optio
       return HS_OK;
     }
   }
-  // candidates: y tile x z chunk (blocks targeted at 512 .. 4096), then the column tile width
+  // candidates: the real-space pass's tiling (FP64: y tile x z chunk; FP32: z chunk of the
+  // column-pair pass, whose rows per block are fixed), blocks targeted at 512 .. 4096; then the
+  // column tile width and the z pass's state staging
   std::vector<hs_options> cands;
-  const int tys[3] = {2, 4, 8};
-  for (int ty : tys) {
+  const bool f32 = (b.precision != HS_FP64) && b.xfuse == 0;
+  for (int ty : {2, 4, 8}) {
     if (grid[1] % ty != 0) continue;
+    if (f32 && ty != 4 && grid[1] % 4 == 0) continue;  // the y tile only shapes the fields pass
     std::vector<int> zcs;
+    const int ytiles = f32 ? grid[1] / xp_groups(grid[0], grid[1]) : grid[1] / ty;
     for (int target : {512, 1024, 2048, 4096}) {
-      const int ytiles = grid[1] / ty;
       const int nz = std::max(1, std::min(grid[2], (target + ytiles - 1) / ytiles));
       const int zc = (grid[2] + nz - 1) / nz;
       if (std::find(zcs.begin(), zcs.end(), zc) == zcs.end()) zcs.push_back(zc);
@@ -1864,6 +1870,7 @@ hs_status hs_autotune(const int grid[3], const hs_material* m_in, const hs_optio
       o.zchunk = zc;
       cands.push_back(o);
     }
+    if (f32) break;
   }
   const double E[6] = {1e-3, 0, 0, 0, 0, 0};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1902,6 +1909,15 @@ hs_status hs_autotune(const int grid[3], const hs_material* m_in, const hs_optio
   {
     hs_options o = win;  // the wider column tile
     o.col_tile = (b.precision == HS_FP64) ? 8 : 16;
+    double t = 0;
+    if (time_one(o, &t) == HS_OK && t < best_t) {
+      best_t = t;
+      win = o;
+    }
+  }
+  for (int cs : {1, 2}) {
+    hs_options o = win;  // the z pass's state staging
+    o.col_state = cs;
     double t = 0;
     if (time_one(o, &t) == HS_OK && t < best_t) {
       best_t = t;

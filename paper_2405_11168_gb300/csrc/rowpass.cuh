@@ -235,16 +235,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
         const T* ra = reinterpret_cast<const T*>(stg + (size_t)(2 * grp) * L.rowbytes);
         const T* rb = reinterpret_cast<const T*>(stg + (size_t)(2 * grp + 1) * L.rowbytes);
         if (a.side != nullptr) {
-          // rows r0, r1 (component c, plane z, row y): a block's top row takes its other part
+          // rows r0, r1 (component c, plane z, row y): a block's top row takes its other part,
+          // read into registers first (at most kE values per thread and row)
           const T* sa = side_row(a, r0);
           const T* sb = side_row(a, r1);
+          T va[kE], vb[kE];
+#pragma unroll
+          for (int k = 0; k < kE; ++k) {
+            const int x = t + k * T8;
+            va[k] = (sa != nullptr && x < n1) ? __ldg(sa + x) : T(0);
+            vb[k] = (sb != nullptr && x < n1) ? __ldg(sb + x) : T(0);
+          }
           T f2 = 0;
-          for (int x = t; x < n1; x += T8) {
-            C w;
-            w.x = ra[x] + (sa ? sa[x] : T(0));
-            w.y = rb[x] + (sb ? sb[x] : T(0));
-            f2 += w.x * w.x + w.y * w.y;
-            z[zi(x)] = w;
+#pragma unroll
+          for (int k = 0; k < kE; ++k) {
+            const int x = t + k * T8;
+            if (x < n1) {
+              C w;
+              w.x = ra[x] + va[k];
+              w.y = rb[x] + vb[k];
+              f2 += w.x * w.x + w.y * w.y;
+              z[zi(x)] = w;
+            }
           }
           kahan1(fsum, fcmp, f2);
         } else {

@@ -44,6 +44,12 @@
 
 namespace hs {
 
+// Planes in flight: the copy of plane p + XP_AHEAD starts when plane p is
+// processed, so a block's short per-plane work does not wait for memory.
+constexpr int XP_AHEAD = 3;
+constexpr int XP_SLOTS = XP_AHEAD + 2;  // corner planes p - 1, p and the ones in flight
+constexpr int XP_BUFS = XP_AHEAD + 1;   // ids and source planes
+
 // Shared memory of k_xpair (host and device use the same function).
 struct XpLayout {
   size_t ring, ids, src, edge, xchg, red, total;
@@ -54,12 +60,12 @@ __host__ __device__ inline XpLayout xp_layout(int n1, int nt, int rg, int ty, bo
   const int R = rg * ty;
   const int nw = (nt + 31) / 32;  // warps per row group
   size_t off = 0;
-  L.ring = off;  // [3 slots][3 comps][R + 1 rows][n1] corner values
-  off += hs_align16((size_t)4 * 3 * 3 * (R + 1) * n1);
-  L.ids = off;  // [2][R][n1] phase ids
-  off += hs_align16((size_t)2 * 2 * R * ((n1 + 7) & ~7));
-  L.src = off;  // [2][3][R][n1] correction source
-  off += hs_align16(has_src ? (size_t)4 * 2 * 3 * R * n1 : 0);
+  L.ring = off;  // [XP_SLOTS][3 comps][R + 1 rows][n1] corner values
+  off += hs_align16((size_t)4 * XP_SLOTS * 3 * (R + 1) * n1);
+  L.ids = off;  // [XP_BUFS][R][n1] phase ids
+  off += hs_align16((size_t)2 * XP_BUFS * R * ((n1 + 7) & ~7));
+  L.src = off;  // [XP_BUFS][3][R][n1] correction source
+  off += hs_align16(has_src ? (size_t)4 * XP_BUFS * 3 * R * n1 : 0);
   L.edge = off;  // [rg][nw][ty + 1][6] left-going sums of each warp's lane 0
   off += hs_align16((size_t)4 * rg * nw * (ty + 1) * 6);
   L.xchg = off;  // [rg][3][n1] a group's part of the corner row below it
@@ -179,12 +185,12 @@ __device__ __forceinline__ void xp_strain(const float2 (&A)[3], const float2 (&B
 }
 
 // Asynchronous copy of one plane: u rows y0 - 1 .. y0 + R - 1 of corner plane
-// pu into ring slot `slot`, ids rows of voxel plane pu into buffer ib, source
-// rows of output plane ps into buffer ib (ps < 0: none).  Warps take rows,
-// lanes the 16-byte chunks of a row.
+// pu into ring slot `slot`, ids rows of voxel plane pu into ids buffer ib (ib < 0:
+// none), source rows of output plane ps into source buffer sb (ps < 0: none).
+// Warps take rows, lanes the 16-byte chunks of a row.  Commits one copy group.
 template <int TY>
 __device__ __forceinline__ void xp_prefetch(const XpArgs& a, const XpLayout& lay, unsigned char* smraw, int R,
-                                            int y0, int pu, int slot, int ib, int ps) {
+                                            int y0, int pu, int slot, int ib, int ps, int sb) {
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const size_t rplane = (size_t)n2 * n1, rcomp = (size_t)n3 * rplane;
@@ -203,18 +209,20 @@ __device__ __forceinline__ void xp_prefetch(const XpArgs& a, const XpLayout& lay
       float* d = dst0 + (size_t)r * n1;
       for (int q = lane; q < nch; q += 32) cp_async16(d + 4 * q, s + 4 * q);
     }
-    uint16_t* di = reinterpret_cast<uint16_t*>(smraw + lay.ids) + (size_t)ib * R * n1i;
-    const uint16_t* si = a.ids + (size_t)gz * rplane;
-    if ((n1 & 7) == 0) {
-      const int nci = n1 >> 3;
-      for (int r = warp; r < R; r += nw)
-        for (int q = lane; q < nci; q += 32) cp_async16(di + r * n1i + 8 * q, si + (size_t)(y0 + r) * n1 + 8 * q);
-    } else {
-      for (int r = warp; r < R; r += nw)
-        for (int q = lane; q < n1; q += 32) di[r * n1i + q] = si[(size_t)(y0 + r) * n1 + q];
+    if (ib >= 0) {
+      uint16_t* di = reinterpret_cast<uint16_t*>(smraw + lay.ids) + (size_t)ib * R * n1i;
+      const uint16_t* si = a.ids + (size_t)gz * rplane;
+      if ((n1 & 7) == 0) {
+        const int nci = n1 >> 3;
+        for (int r = warp; r < R; r += nw)
+          for (int q = lane; q < nci; q += 32) cp_async16(di + r * n1i + 8 * q, si + (size_t)(y0 + r) * n1 + 8 * q);
+      } else {
+        for (int r = warp; r < R; r += nw)
+          for (int q = lane; q < n1; q += 32) di[r * n1i + q] = si[(size_t)(y0 + r) * n1 + q];
+      }
     }
     if (a.src != nullptr && ps >= 0) {
-      float* ds = reinterpret_cast<float*>(smraw + lay.src) + (size_t)ib * 3 * R * n1;
+      float* ds = reinterpret_cast<float*>(smraw + lay.src) + (size_t)sb * 3 * R * n1;
       const float* s0 = a.src + (size_t)ps * rplane;
       for (int r = warp; r < 3 * R; r += nw) {
         const int c = r / R, rr = r - c * R;
@@ -229,12 +237,14 @@ __device__ __forceinline__ void xp_prefetch(const XpArgs& a, const XpLayout& lay
       const int gy = (y0 - 1 + j + n2) % n2;
       for (int q = lane; q < n1; q += 32) dst0[(size_t)r * n1 + q] = srcz[c * rcomp + (size_t)gy * n1 + q];
     }
-    uint16_t* di = reinterpret_cast<uint16_t*>(smraw + lay.ids) + (size_t)ib * R * n1i;
-    const uint16_t* si = a.ids + (size_t)gz * rplane;
-    for (int r = warp; r < R; r += nw)
-      for (int q = lane; q < n1; q += 32) di[r * n1i + q] = si[(size_t)(y0 + r) * n1 + q];
+    if (ib >= 0) {
+      uint16_t* di = reinterpret_cast<uint16_t*>(smraw + lay.ids) + (size_t)ib * R * n1i;
+      const uint16_t* si = a.ids + (size_t)gz * rplane;
+      for (int r = warp; r < R; r += nw)
+        for (int q = lane; q < n1; q += 32) di[r * n1i + q] = si[(size_t)(y0 + r) * n1 + q];
+    }
     if (a.src != nullptr && ps >= 0) {
-      float* ds = reinterpret_cast<float*>(smraw + lay.src) + (size_t)ib * 3 * R * n1;
+      float* ds = reinterpret_cast<float*>(smraw + lay.src) + (size_t)sb * 3 * R * n1;
       const float* s0 = a.src + (size_t)ps * rplane;
       for (int r = warp; r < 3 * R; r += nw) {
         const int c = r / R, rr = r - c * R;
@@ -304,21 +314,34 @@ __global__ void __launch_bounds__(512) k_xpair(const XpArgs a_, const MAT mat_) 
 #pragma unroll
   for (int i = 0; i < 6; ++i) ssum[i] = scmp[i] = make_float2(0.f, 0.f);
 
-  xp_prefetch<TY>(a, lay, smraw, R, y0, z0 - 1, 0, 0, -1);
-  xp_prefetch<TY>(a, lay, smraw, R, y0, z0, 1, 0, -1);
+  // pipeline: corner plane q in ring slot (q - z0 + 1) % XP_SLOTS, ids of voxel plane q in
+  // buffer (q - z0) % XP_BUFS, source of output plane q in buffer (q - z0) % XP_BUFS; one
+  // copy group per plane (empty past the chunk), so that plane p is complete once at most
+  // XP_AHEAD - 1 later groups are pending
   const int pend = z0 + zc;
+  xp_prefetch<TY>(a, lay, smraw, R, y0, z0 - 1, 0, -1, -1, 0);
+  for (int q = z0; q < z0 + XP_AHEAD - 1; ++q) {
+    if (q <= pend) xp_prefetch<TY>(a, lay, smraw, R, y0, q, (q - z0 + 1) % XP_SLOTS, (q - z0) % XP_BUFS,
+                                   q - 1 >= z0 ? q - 1 : -1, (q - 1 - z0 + XP_BUFS) % XP_BUFS);
+    else cp_async_commit();
+  }
   for (int p = z0; p <= pend; ++p) {
-    const int ib = (p - z0) & 1;
-    cp_async_wait_all();
-    __syncthreads();
-    const int sc = (p - z0 + 1) % 3, sp = (p - z0) % 3;
-    // the previous step's edge and xchg reads are done (barrier above): prefetch the next plane
-    // into the slot that held plane p - 2
-    if (p < pend) xp_prefetch<TY>(a, lay, smraw, R, y0, p + 1, (p - z0 + 2) % 3, ib ^ 1, p);
+    {
+      // plane p + XP_AHEAD - 1 goes into the slot of plane p - 3 (its ids and source buffers held
+      // planes p - 2 and p - 3): all were last read during step p - 2, before the barriers of
+      // step p - 1; then wait for plane p
+      const int q = p + XP_AHEAD - 1;
+      if (q <= pend) xp_prefetch<TY>(a, lay, smraw, R, y0, q, (q - z0 + 1) % XP_SLOTS, (q - z0) % XP_BUFS, q - 1,
+                                     (q - 1 - z0) % XP_BUFS);
+      else cp_async_commit();
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(XP_AHEAD - 1) : "memory");
+      __syncthreads();
+    }
+    const int sc = (p - z0 + 1) % XP_SLOTS, sp = (p - z0) % XP_SLOTS;
     const bool own_plane = p < z0 + zc;
     const float* rc = ring + (size_t)sc * 3 * NRW * n1;  // corner plane p
     const float* rp = ring + (size_t)sp * 3 * NRW * n1;  // corner plane p - 1
-    const uint16_t* idp = sids + (size_t)ib * R * n1i;
+    const uint16_t* idp = sids + (size_t)((p - z0) % XP_BUFS) * R * n1i;
 
     float2 pls[6];
 #pragma unroll
@@ -489,7 +512,7 @@ __global__ void __launch_bounds__(512) k_xpair(const XpArgs a_, const MAT mat_) 
           for (int k = 0; k < 3; ++k)
             *reinterpret_cast<float2*>(a.side + (size_t)k * n3 * (n2 / R) * n1 + so) = p2mul(q, Fp[0][k]);
         }
-        const float* sr = ssrc + (size_t)ib * 3 * R * n1;
+        const float* sr = ssrc + (size_t)((p - 1 - z0) % XP_BUFS) * 3 * R * n1;
 #pragma unroll
         for (int r = 1; r <= TY; ++r) {
           const int yr = y0 + g * TY + r - 1;
