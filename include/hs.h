@@ -114,8 +114,8 @@ hs_status hs_default_options(hs_options* opt);
 
 /* Autotuner with a process-wide plan cache (no counterpart in the paper: it picks launch
  * shapes, not numerics).  Times `iters` evaluations of each candidate tiling of the
- * real-space and FFT passes (HS_FP64: y tile 2/4/8 x z chunk; FP32 modes: the z chunk of
- * the column-pair pass; then the wider column tile and the z pass's col_state) with
+ * real-space and FFT passes (y tile 2/4/8 x z chunk, then the wider column tile and the z
+ * pass's col_state) with
  * CUDA events on `stream`, using the caller's workspace (hs_workspace_size bytes for
  * `base`), and writes the fastest options to *best (*best_ms: ms per evaluation, or -1
  * when the plan came from the cache).  Results do not depend on the tiling beyond

@@ -186,19 +186,8 @@ bool cholesky_pd(const double* A) {
 }
 
 struct Layout {
-  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, c0, side, rpart, u64, rsrc,
-      total;
+  size_t S, B0, B1, F, ids, matk, matd, tw, partials, status, hist, macro, sig0f, sig0d, c0, u64, rsrc, total;
 };
-
-// Row groups (one voxel row each) per block of the FP32 column-pair pass: up to
-// 8 groups of round-up(N1/2, 32) threads within 512 threads, dividing N2.
-int xp_groups(int n1, int n2) {
-  const int nt = ((n1 / 2 + 31) / 32) * 32;
-  int rg = std::min(8, 512 / nt);
-  while (rg > 1 && n2 % rg != 0) rg /= 2;
-  return rg;
-}
-constexpr int kMaxRowBlocks = 4096;  // per-block |F|^2 sums of the forward x pass
 
 }  // namespace
 
@@ -221,13 +210,6 @@ struct hs_ctx {
   int batch_n = 1;
   size_t batch_stride = 0;
   int layout_np = 1;        // phase count the workspace layout was sized for (>= nphase)
-  // FP32 iterations (xfuse = 0): the column-pair real-space pass k_xpair
-  bool xp = false;
-  int xp_rg = 0, xp_nthr = 0, xp_zc = 0;
-  dim3 grid_xp;
-  size_t smem_xp = 0, smem_xp_src = 0;
-  float* side = nullptr;
-  double* rpart = nullptr;
   bool unbound = false;     // a failed hs_set_material left the workspace without a valid material
   char* ws;
   size_t ws_bytes;
@@ -535,9 +517,6 @@ Layout make_layout(int n1, int n2, int n3, int nphase, int prec) {
   L.sig0f = off; off += align256((size_t)nphase * 6 * 4);
   L.sig0d = off; off += align256((size_t)nphase * 6 * 8);
   L.c0 = off; off += align256(32);  // isotropic reference medium (lambda0 + mu0, mu0): 2 double, then 2 float
-  // FP32 iterations: the column-pair pass's partial rows at block boundaries, the row pass's sums
-  L.side = off; off += f64 ? 0 : align256((size_t)3 * n3 * (n2 / xp_groups(n1, n2)) * n1 * 4);
-  L.rpart = off; off += f64 ? 0 : align256((size_t)kMaxRowBlocks * 8);
   L.u64 = off;
   L.rsrc = off;
   if (prec == HS_FP32_REFINED) {
@@ -634,19 +613,6 @@ template <typename T> hs_status launch_rows(hs_ctx* c, int mode, double* acc64, 
   a.st = c->st;
   a.skip_if_done = skip ? 1 : 0;
   a.zstride = c->batch_stride;
-  if constexpr (std::is_same<T, float>::value) {
-    if (c->xp && mode == hs::ROW_R2C) {
-      // complete the rows the column-pair pass left partial, sum |F|^2, take the stopping test
-      a.side = c->side;
-      a.srows = c->xp_rg;
-      a.n2 = c->n2;
-      a.n3 = c->n3;
-      a.spart = c->partials;
-      a.nspart = (int)(c->grid_xp.x * c->grid_xp.y);
-      a.rpart = c->rpart;
-      a.hist = c->hist;
-    }
-  }
   cudaError_t e;
   {
     LaunchScope ls(c, acc64 ? HS_K_OTHER : (mode == hs::ROW_C2R ? HS_K_XINV : HS_K_XFWD));
@@ -685,43 +651,6 @@ template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], con
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_march(real)");
   return HS_OK;
-}
-
-// the real-space pass of one iteration: k_xpair for FP32, k_march for FP64
-template <typename T> hs_status launch_xpass(hs_ctx* c, const double E[6], const float* src) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (c->xp) {
-      hs::XpArgs a;
-      memset(&a, 0, sizeof(a));
-      a.ureal = (const float*)c->B[1];
-      a.ids = c->ids;
-      a.mat = (const float*)c->matk;
-      a.fout = (float*)c->F;
-      a.side = c->side;
-      a.src = src;
-      a.partials = c->partials;
-      a.st = c->st;
-      // the correction equation K du = -r is linear: no eigenstrain, macro strain 0
-      a.Edev = src != nullptr ? nullptr : &c->st->E[0];
-      a.sig0 = (src != nullptr || !c->has_eigen) ? nullptr : c->sig0f;
-      for (int i = 0; i < 6; ++i) a.E[i] = src != nullptr ? 0.f : (float)E[i];
-      a.n1 = c->n1;
-      a.n2 = c->n2;
-      a.n3 = c->n3;
-      a.zc = c->xp_zc;
-      a.skip_if_done = 1;
-      a.zstride = c->batch_stride;
-      cudaError_t e;
-      {
-        LaunchScope ls(c, src != nullptr ? HS_K_XPASS_SRC : HS_K_XPASS);
-        e = hs::launch_xpair(a, c->iso, 1, zg(c, c->grid_xp), c->xp_nthr, src != nullptr ? c->smem_xp_src : c->smem_xp,
-                             c->stream);
-      }
-      if (e != cudaSuccess) return cuda_fail(c, e, "k_xpair");
-      return HS_OK;
-    }
-  }
-  return launch_stencil<T>(c, E, src, hs::MODE_FORCE, nullptr, nullptr);
 }
 
 template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
@@ -860,7 +789,7 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
         cur ^= 1;
       } else {
         hs_status s = launch_rows<T>(c, hs::ROW_C2R, nullptr, true);
-        if (s == HS_OK) s = launch_xpass<T>(c, E, src);
+        if (s == HS_OK) s = launch_stencil<T>(c, E, src, hs::MODE_FORCE, nullptr, nullptr);
         if (s == HS_OK) s = launch_rows<T>(c, hs::ROW_R2C, nullptr, true);
         if (s == HS_OK) s = launch_cols<T>(c, 0);
         if (s != HS_OK) {
@@ -929,9 +858,7 @@ hs_status solve_plain(hs_ctx* c, const double E[6], double tol, int max_iter, vo
     if (c->xfuse) {
       s = launch_fields<T>(c, E, last_in, eps, sig);
     } else {
-      // B[1] still holds the real displacement of the last evaluation when the column-pair pass
-      // ran it (its stopping test, in the forward x pass, let that pass overwrite B[0])
-      s = c->xp ? HS_OK : launch_rows<T>(c, hs::ROW_C2R, nullptr, false);
+      s = launch_rows<T>(c, hs::ROW_C2R, nullptr, false);
       if (s == HS_OK) s = launch_stencil<T>(c, E, nullptr, hs::MODE_FIELDS, eps, sig);
     }
     if (s != HS_OK) return s;
@@ -1303,8 +1230,6 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
   c->macro = (double*)(c->ws + c->lay.macro);
   c->sig0f = (float*)(c->ws + c->lay.sig0f);
   c->sig0d = (double*)(c->ws + c->lay.sig0d);
-  c->side = c->f64 ? nullptr : (float*)(c->ws + c->lay.side);
-  c->rpart = c->f64 ? nullptr : (double*)(c->ws + c->lay.rpart);
   c->u64 = (o.precision == HS_FP32_REFINED) ? (double*)(c->ws + c->lay.u64) : nullptr;
   c->rsrc = (o.precision == HS_FP32_REFINED) ? (float*)(c->ws + c->lay.rsrc) : nullptr;
   c->warm = false;
@@ -1377,25 +1302,6 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
     delete c;
     return st;
   }
-  // FP32 iterations: the column-pair pass, row groups of round-up(N1/2, 32) threads
-  if (!c->f64 && !c->xfuse) {
-    c->xp = true;
-    c->xp_rg = xp_groups(c->n1, c->n2);
-    c->xp_nthr = c->xp_rg * (((c->n1 / 2 + 31) / 32) * 32);
-    const int yt = c->n2 / c->xp_rg;
-    int nz = std::max(1, std::min(c->n3, (kTargetBlocks + yt - 1) / yt));
-    c->xp_zc = (c->n3 + nz - 1) / nz;
-    if (o.zchunk > 0) c->xp_zc = std::min(o.zchunk, c->n3);
-    nz = (c->n3 + c->xp_zc - 1) / c->xp_zc;
-    c->grid_xp = dim3(yt, nz);
-    const int nt = ((c->n1 / 2 + 31) / 32) * 32;
-    c->smem_xp = hs::xp_layout(c->n1, nt, c->xp_rg, 1, false).total;
-    c->smem_xp_src = hs::xp_layout(c->n1, nt, c->xp_rg, 1, true).total;
-    if ((size_t)yt * nz > (size_t)((c->n2 / 2) * c->n3) || c->smem_xp_src > (size_t)smem_optin) {
-      delete c;
-      return fail(nullptr, HS_ERR_UNSUPPORTED_SIZE, "grid too large for the column-pair pass");
-    }
-  }
   // real-space pass: an automatic row tile is halved while its plane ring does not fit
   // (FP64 rows of 512 need 2 rows per block)
   if (o.ytile == 0 && !c->xfuse) {
@@ -1449,8 +1355,7 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       int per_sm = 0;
       e = c->f64 ? hs::row_blocks_per_sm<double>(m, c->n1, c->nthr_row, c->smem_row[m], &per_sm)
                  : hs::row_blocks_per_sm<float>(m, c->n1, c->nthr_row, c->smem_row[m], &per_sm);
-      c->nblk_row[m] = (int)std::min<size_t>({nbatch, (size_t)std::max(1, per_sm) * std::max(1, nsm),
-                                              (size_t)kMaxRowBlocks});
+      c->nblk_row[m] = (int)std::min<size_t>(nbatch, (size_t)std::max(1, per_sm) * std::max(1, nsm));
     }
     if (e != cudaSuccess) {
       hs_status st = cuda_fail(nullptr, e, "row pass occupancy");
@@ -1849,16 +1754,13 @@ hs_status hs_autotune(const int grid[3], const hs_material* m_in, const hs_optio
       return HS_OK;
     }
   }
-  // candidates: the real-space pass's tiling (FP64: y tile x z chunk; FP32: z chunk of the
-  // column-pair pass, whose rows per block are fixed), blocks targeted at 512 .. 4096; then the
-  // column tile width and the z pass's state staging
+  // candidates: y tile x z chunk of the real-space pass (blocks targeted at 512 .. 4096), then
+  // the column tile width and the z pass's state staging
   std::vector<hs_options> cands;
-  const bool f32 = (b.precision != HS_FP64) && b.xfuse == 0;
   for (int ty : {2, 4, 8}) {
     if (grid[1] % ty != 0) continue;
-    if (f32 && ty != 4 && grid[1] % 4 == 0) continue;  // the y tile only shapes the fields pass
     std::vector<int> zcs;
-    const int ytiles = f32 ? grid[1] / xp_groups(grid[0], grid[1]) : grid[1] / ty;
+    const int ytiles = grid[1] / ty;
     for (int target : {512, 1024, 2048, 4096}) {
       const int nz = std::max(1, std::min(grid[2], (target + ytiles - 1) / ytiles));
       const int zc = (grid[2] + nz - 1) / nz;
@@ -1870,7 +1772,6 @@ hs_status hs_autotune(const int grid[3], const hs_material* m_in, const hs_optio
       o.zchunk = zc;
       cands.push_back(o);
     }
-    if (f32) break;
   }
   const double E[6] = {1e-3, 0, 0, 0, 0, 0};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2213,7 +2114,7 @@ template <typename T> hs_status batch_iterate(hs_batch* b, bool with_src) {
   auto one_chunk = [&](hs_ctx* L) -> hs_status {
     for (int i = 0; i < chunk; ++i) {
       hs_status s = launch_rows<T>(L, hs::ROW_C2R, nullptr, true);
-      if (s == HS_OK) s = launch_xpass<T>(L, zeroE, with_src ? L->rsrc : nullptr);
+      if (s == HS_OK) s = launch_stencil<T>(L, zeroE, with_src ? L->rsrc : nullptr, hs::MODE_FORCE, nullptr, nullptr);
       if (s == HS_OK) s = launch_rows<T>(L, hs::ROW_R2C, nullptr, true);
       if (s == HS_OK) s = launch_cols<T>(L, 0);
       if (s != HS_OK) return s;

@@ -94,16 +94,30 @@ static cudaError_t stencil_one(const MarchArgs<float>& a, const MATP& m, dim3 g,
 template <int TY>
 static cudaError_t stencil_ty(const MarchArgs<float>& a, bool iso, int mode, dim3 g, int nthr, size_t smem,
                               cudaStream_t s) {
-  if (iso) return stencil_one<TY, MatIsoP, MODE_FIELDS>(a, MatIsoP{a.mat}, g, nthr, smem, s);
-  return stencil_one<TY, MatAnisoP, MODE_FIELDS>(a, MatAnisoP{a.mat}, g, nthr, smem, s);
+  if (iso) {
+    MatIsoP m{a.mat};
+    if constexpr (TY == 4) {
+      if (mode == MODE_FORCE && a.n1 == 256 && nthr == 256)
+        return stencil_one<TY, MatIsoP, MODE_FORCE, 256>(a, m, g, nthr, smem, s);
+    }
+    if (mode == MODE_FORCE) return stencil_one<TY, MatIsoP, MODE_FORCE>(a, m, g, nthr, smem, s);
+    return stencil_one<TY, MatIsoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
+  }
+  MatAnisoP m{a.mat};
+  if constexpr (TY == 4) {
+    if (mode == MODE_FORCE && a.n1 == 256 && nthr == 256)
+      return stencil_one<TY, MatAnisoP, MODE_FORCE, 256>(a, m, g, nthr, smem, s);
+  }
+  if (mode == MODE_FORCE) return stencil_one<TY, MatAnisoP, MODE_FORCE>(a, m, g, nthr, smem, s);
+  return stencil_one<TY, MatAnisoP, MODE_FIELDS>(a, m, g, nthr, smem, s);
 }
 
-// FP32 fields pass (MODE_FIELDS on a real displacement field; the FP32 iterations run the
-// column-pair pass k_xpair); a template so that only the unit that launches it instantiates it
+// FP32 real-space pass (FORCE / FIELDS on a real displacement field); a
+// template so that only the unit that launches it instantiates its kernels
 template <int UNUSED = 0>
 static cudaError_t stencil_f32(const MarchArgs<float>& a, bool iso, int ty, int mode, dim3 g, int nthr,
                                size_t smem, cudaStream_t s) {
-  if (mode != MODE_FIELDS) return cudaErrorInvalidValue;
+  if (mode != MODE_FORCE && mode != MODE_FIELDS) return cudaErrorInvalidValue;
   switch (ty) {
     case 2: return stencil_ty<2>(a, iso, mode, g, nthr, smem, s);
     case 4: return stencil_ty<4>(a, iso, mode, g, nthr, smem, s);

@@ -7,7 +7,6 @@
 #include "march.cuh"
 #include "rowpass.cuh"
 #include "stencil.cuh"
-#include "xpair.cuh"
 
 namespace hs {
 
@@ -35,12 +34,6 @@ cudaError_t row_blocks_per_sm_ext(int mode, int nthr, size_t smem, int* n);
 // resident blocks per SM of the row pass (persistent grid sizing)
 template <typename T>
 cudaError_t row_blocks_per_sm(int mode, int n1, int nthr, size_t smem, int* n);
-
-// FP32 column-pair real-space pass (k_xpair, MODE_FORCE): grid (n2 / (rg * ty), z chunks[, items]),
-// rg * nt threads (nt = round-up(n1 / 2, 32)), ty = 1
-cudaError_t launch_xpair(const XpArgs& a, bool iso, int ty, dim3 grid, int nthr, size_t smem, cudaStream_t s);
-// occupancy of k_xpair (blocks per SM)
-cudaError_t xpair_blocks_per_sm(bool iso, int ty, int nthr, size_t smem, int* n);
 
 // u8 phase ids -> u16
 cudaError_t launch_ids_u8_to_u16(const uint8_t* in, uint16_t* out, size_t n, cudaStream_t s);

@@ -29,19 +29,9 @@ template <typename T> struct RowArgs {
   const C* tw;        // w_N1^j
   FftPlan plan;
   int n1, P, nrows;
-  DevStatus* st;
+  const DevStatus* st;
   int skip_if_done;
   size_t zstride;     // batched launches: bytes between the workspaces of consecutive items
-  // R2C after the column-pair stencil pass (k_xpair): the input rows are [3][n3][n2], row y of
-  // each (component, plane) with (y + 1) % srows == 0 lacks the part that side[((y + 1) % n2) /
-  // srows] holds, and this pass completes it, sums |F|^2 and (last block) takes the stopping test
-  // from spart (nspart blocks of NRED sums of sigma) and its own per-block sums rpart.
-  const T* side;
-  int srows, n2, n3;
-  const double* spart;
-  int nspart;
-  double* rpart;
-  double* hist;
 };
 
 template <typename T> __device__ __forceinline__ RowArgs<T> row_item_args(const RowArgs<T>& a) {
@@ -55,10 +45,6 @@ template <typename T> __device__ __forceinline__ RowArgs<T> row_item_args(const 
   b.acc64 = zshift(a.acc64, o);
   b.tw = zshift(a.tw, o);
   b.st = zshift(a.st, o);
-  b.side = zshift(a.side, o);
-  b.spart = zshift(a.spart, o);
-  b.rpart = zshift(a.rpart, o);
-  b.hist = zshift(a.hist, o);
   return b;
 }
 
@@ -115,23 +101,6 @@ __device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& 
   cp_async_commit();
 }
 
-// The side row that completes input row r of an R2C pass after k_xpair, or null.
-template <typename T> __device__ __forceinline__ const T* side_row(const RowArgs<T>& a, size_t r) {
-  const int y = (int)(r % (size_t)a.n2);
-  if ((y + 1) % a.srows != 0) return nullptr;
-  const size_t cz = r / (size_t)a.n2;  // component * n3 + plane
-  const int nby = a.n2 / a.srows;
-  return a.side + (cz * nby + ((y + 1) % a.n2) / a.srows) * (size_t)a.n1;
-}
-
-// compensated scalar accumulation (Kahan): s + c holds the running sum
-template <typename T> __device__ __forceinline__ void kahan1(T& s, T& c, T x) {
-  const T y = x - c;
-  const T t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 // Persistent: block j transforms batches j, j + gridDim.x, ...; the copy of the
 // next batch runs while the current one is transformed.
 // LF > 0: N1 = LF and 256 threads per block, fixed at compile time (hot
@@ -165,7 +134,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
   // updates).  R2C measured faster with direct stores (0.104 vs 0.112 ms at 256^3).
   const bool bulk = LF > 0 && MODE == ROW_C2R && a.acc64 == nullptr && (L.outbytes & 15) == 0;
   int buf = 0;
-  T fsum = 0, fcmp = 0;  // this thread's sum of |F|^2 (compensated)
   if ((int)blockIdx.x < nbatch) row_stage<T, MODE>(a, L, smraw, blockIdx.x, 0);
   for (int b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
     cp_async_wait_all();
@@ -234,39 +202,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       if (act) {
         const T* ra = reinterpret_cast<const T*>(stg + (size_t)(2 * grp) * L.rowbytes);
         const T* rb = reinterpret_cast<const T*>(stg + (size_t)(2 * grp + 1) * L.rowbytes);
-        if (a.side != nullptr) {
-          // rows r0, r1 (component c, plane z, row y): a block's top row takes its other part,
-          // read into registers first (at most kE values per thread and row)
-          const T* sa = side_row(a, r0);
-          const T* sb = side_row(a, r1);
-          T va[kE], vb[kE];
-#pragma unroll
-          for (int k = 0; k < kE; ++k) {
-            const int x = t + k * T8;
-            va[k] = (sa != nullptr && x < n1) ? __ldg(sa + x) : T(0);
-            vb[k] = (sb != nullptr && x < n1) ? __ldg(sb + x) : T(0);
-          }
-          T f2 = 0;
-#pragma unroll
-          for (int k = 0; k < kE; ++k) {
-            const int x = t + k * T8;
-            if (x < n1) {
-              C w;
-              w.x = ra[x] + va[k];
-              w.y = rb[x] + vb[k];
-              f2 += w.x * w.x + w.y * w.y;
-              z[zi(x)] = w;
-            }
-          }
-          kahan1(fsum, fcmp, f2);
-        } else {
 #pragma unroll 4
-          for (int x = t; x < n1; x += T8) {
-            C w;
-            w.x = ra[x];
-            w.y = rb[x];
-            z[zi(x)] = w;
-          }
+        for (int x = t; x < n1; x += T8) {
+          C w;
+          w.x = ra[x];
+          w.y = rb[x];
+          z[zi(x)] = w;
         }
       }
       group_sync(wsync);
@@ -321,26 +262,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
   }
   cp_async_wait_all();
   if (bulk && tid == 0) bulk_wait_all();
-  if (MODE == ROW_R2C && a.side != nullptr) {
-    // sum |F|^2 per block (FP64), then the last block takes the stopping test
-    __shared__ double scratch[32 * NRED];
-    double acc[1] = {(double)fsum - (double)fcmp};
-    block_sum<1>(acc, a.rpart + blockIdx.x, scratch);
-    if (!last_block_arrived(a.st, gridDim.x)) return;
-    const int lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
-    for (int v = warp; v < NRED; v += nw) {
-      double sv = 0;
-      if (v < 6) {
-        for (int b = lane; b < a.nspart; b += 32) sv += __ldcg(a.spart + (size_t)b * NRED + v);
-      } else if (v == 6) {
-        for (int b = lane; b < (int)gridDim.x; b += 32) sv += __ldcg(a.rpart + b);
-      }
-      sv = warp_sum(sv);
-      if (lane == 0) scratch[v] = sv;
-    }
-    __syncthreads();
-    if (tid == 0) finalize_eval(a.st, a.hist, scratch);
-  }
 }
 
 }  // namespace hs

@@ -1,7 +1,5 @@
 // FP32 real-space pass of the basic scheme: strain stencil, constitutive step
-// and adjoint stencil on a real displacement field, marching along z.  The
-// launchers instantiate it for MODE_FIELDS (the strain and stress fields of an
-// FP32 solve); the force of the FP32 iterations comes from k_xpair (xpair.cuh).
+// and adjoint stencil on a real displacement field, marching along z.
 //
 // Same contract as k_march with REAL = true (see march.cuh for the tiling and
 // the plane/row conventions), organised for instruction count:
