@@ -105,11 +105,14 @@ typedef struct {
   int col_state;        /* z pass + Green update: 0 = automatic, 1 = state read point by point (L2
                            prefetch), 2 = state tile copied to shared memory during the forward z
                            transform (twice the tile's shared memory); results do not change */
+  int col_pipe;         /* y and z passes at lengths 128, 256, 512 with the default tile: 0 = persistent
+                           blocks that copy the next tile while transforming the current one
+                           (default), 1 = one tile per block; results do not change */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,
  * inner_max 200, inner_ratio 1e-3, zchunk 0, ytile 0, xfuse 0, col_tile 0, col_threads 0,
- * use_graphs 1, col_state 0. */
+ * use_graphs 1, col_state 0, col_pipe 0. */
 hs_status hs_default_options(hs_options* opt);
 
 /* Autotuner with a process-wide plan cache (no counterpart in the paper: it picks launch

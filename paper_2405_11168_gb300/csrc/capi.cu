@@ -250,6 +250,10 @@ struct hs_ctx {
   size_t smem_row[2];
   size_t smem_y, smem_z;
   bool zstate_smem = false;  // the z pass copies the state tile to shared memory
+  // persistent double-buffered y / z passes (k_colp): blocks and shared memory
+  bool pipe_y = false, pipe_z = false;
+  int nblk_py = 0, nblk_pz = 0;
+  size_t smem_py = 0, smem_pz = 0;
   dim3 grid_y, grid_z;
   bool warm;
   int cur;
@@ -659,19 +663,23 @@ template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   fill_col<T>(c, a, c->B[buf], 1);
   {
     LaunchScope ls(c, HS_K_YFWD);
-    e = hs::launch_col<T>(a, hs::COL_Y_FWD, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
+    e = c->pipe_y ? hs::launch_colp<T>(a, hs::COL_Y_FWD, c->ct, zg(c, dim3(c->nblk_py)), c->nthr_y, c->smem_py, c->stream)
+                  : hs::launch_col<T>(a, hs::COL_Y_FWD, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y fwd)");
   fill_col<T>(c, a, c->B[buf], 2);
   {
     LaunchScope ls(c, HS_K_ZGREEN);
-    e = hs::launch_col<T>(a, hs::COL_Z_GREEN, c->ct, zg(c, c->grid_z), c->nthr_z, c->smem_z, c->stream);
+    e = c->pipe_z ? hs::launch_colp<T>(a, hs::COL_Z_GREEN, c->ct, zg(c, dim3(c->nblk_pz)), c->nthr_z, c->smem_pz,
+                                       c->stream)
+                  : hs::launch_col<T>(a, hs::COL_Z_GREEN, c->ct, zg(c, c->grid_z), c->nthr_z, c->smem_z, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z green)");
   fill_col<T>(c, a, c->B[buf], 1);
   {
     LaunchScope ls(c, HS_K_YINV);
-    e = hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
+    e = c->pipe_y ? hs::launch_colp<T>(a, hs::COL_Y_INV, c->ct, zg(c, dim3(c->nblk_py)), c->nthr_y, c->smem_py, c->stream)
+                  : hs::launch_col<T>(a, hs::COL_Y_INV, c->ct, zg(c, c->grid_y), c->nthr_y, c->smem_y, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y inv)");
   return HS_OK;
@@ -1073,6 +1081,7 @@ hs_status hs_default_options(hs_options* opt) {
   opt->col_threads = 0;
   opt->use_graphs = 1;
   opt->col_state = 0;
+  opt->col_pipe = 0;
   return HS_OK;
 }
 
@@ -1117,7 +1126,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       !(o.inner_ratio > 0 && o.inner_ratio < 1) || o.zchunk < 0 ||
       !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
       (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0 ||
-      (o.use_graphs != 0 && o.use_graphs != 1) || o.col_state < 0 || o.col_state > 2)
+      (o.use_graphs != 0 && o.use_graphs != 1) || o.col_state < 0 || o.col_state > 2 ||
+      (o.col_pipe != 0 && o.col_pipe != 1))
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > HS_MAX_PHASES)
@@ -1361,6 +1371,42 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       hs_status st = cuda_fail(nullptr, e, "row pass occupancy");
       delete c;
       return st;
+    }
+  }
+
+  // persistent double-buffered y / z passes at the compile-time lengths (default tile and block)
+  {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const bool ext = hs::plan_ext(c->plan[1]) || hs::plan_ext(c->plan[2]);
+    const int xtiles = (c->nh + c->ct - 1) / c->ct;
+    for (int axis = 1; axis <= 2 && o.col_pipe == 0 && !ext && nsm > 0; ++axis) {
+      const int L = axis == 1 ? c->n2 : c->n3;
+      if (axis == 2 && c->zstate_smem) continue;
+      if (L != 128 && L != 256 && L != 512) continue;
+      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs;
+      if (smem > (size_t)smem_optin) continue;
+      const int nthr = axis == 1 ? c->nthr_y : c->nthr_z;
+      int per_sm = 0;
+      cudaError_t q = c->f64 ? hs::colp_blocks_per_sm<double>(axis == 1 ? hs::COL_Y_FWD : hs::COL_Z_GREEN, L, c->ct, nthr,
+                                                              smem, &per_sm)
+                             : hs::colp_blocks_per_sm<float>(axis == 1 ? hs::COL_Y_FWD : hs::COL_Z_GREEN, L, c->ct, nthr,
+                                                             smem, &per_sm);
+      if (q != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        continue;
+      }
+      const size_t ntiles = (size_t)xtiles * (axis == 1 ? c->n3 : c->n2);
+      const int nb = (int)std::min<size_t>(ntiles, (size_t)per_sm * nsm);
+      if (axis == 1) {
+        c->pipe_y = true;
+        c->nblk_py = nb;
+        c->smem_py = smem;
+      } else {
+        c->pipe_z = true;
+        c->nblk_pz = nb;
+        c->smem_pz = smem;
+      }
     }
   }
 

@@ -285,4 +285,81 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   }
 }
 
+// Persistent column pass for the compile-time lengths: block j transforms tiles j,
+// j + gridDim.x, ... (tile t: x columns (t mod xtiles) * CT, outer index t / xtiles)
+// and copies the next tile into its second buffer while it transforms the current
+// one, so the copies overlap the arithmetic.  Y_FWD, Y_INV and Z_GREEN (state read
+// point by point after an L2 prefetch issued with the tile's copy).
+template <typename T, int CT, int MODE, int LF, int NT>
+__global__ void __launch_bounds__(NT, 2) k_colp(const ColArgs<T> a_) {
+  using C = typename cplx_t<T>::type;
+  static_assert(LF > 0 && MODE != COL_Z_INV_STATE, "persistent column pass: fixed lengths, iteration modes");
+  const ColArgs<T> a = col_item_args(a_);
+  if (a.st->retired || (a.skip_if_done && a.st->done)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr bool yaxis = (MODE == COL_Y_FWD || MODE == COL_Y_INV);
+  constexpr int L = LF, W = 3 * CT;
+  constexpr int EPC = 16 / (int)sizeof(C);
+  constexpr int CPR = CT / EPC;
+  C* const sm0 = reinterpret_cast<C*>(smraw);  // [2][L][3][CT]
+  const int tid = threadIdx.x;
+  const size_t plane = (size_t)a.n2 * a.P;
+  const size_t cstride = (size_t)a.n3 * plane;
+  const size_t rstride = yaxis ? (size_t)a.P : plane;
+  const int xtiles = (a.nh + CT - 1) / CT;
+  const int ntiles = xtiles * (yaxis ? a.n3 : a.n2);
+  const C* __restrict__ tw = a.tw;
+  auto load = [&](int t, C* sm) {
+    const int x0 = (t % xtiles) * CT, outer = t / xtiles;
+    const size_t base = yaxis ? (size_t)outer * plane + x0 : (size_t)outer * a.P + x0;
+    const int ccols = min(CT, a.P - x0);
+    for (int i = tid; i < L * 3 * CPR; i += NT) {
+      const int e = i / (3 * CPR), rem = i - e * (3 * CPR), c = rem / CPR, col = (rem - c * CPR) * EPC;
+      C* dst = sm + e * W + c * CT + col;
+      if (col < ccols) {
+        cp_async16(dst, a.buf + c * cstride + base + e * rstride + col);
+      } else {
+#pragma unroll
+        for (int q = 0; q < EPC; ++q) dst[q] = cmk<C>(0, 0);
+      }
+    }
+    if (MODE == COL_Z_GREEN) {
+      for (int i = tid; i < L * 3; i += NT) {
+        const int e = i / 3, c = i - 3 * e;
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
+      }
+    }
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) load(t, sm0);
+  cp_async_commit();
+  for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
+    C* sm = sm0 + (size_t)(k & 1) * L * W;
+    // the other buffer was freed by the barrier that ended the previous tile
+    if (t + (int)gridDim.x < ntiles) load(t + gridDim.x, sm0 + (size_t)((k + 1) & 1) * L * W);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    const int x0 = (t % xtiles) * CT, outer = t / xtiles;
+    const size_t base = yaxis ? (size_t)outer * plane + x0 : (size_t)outer * a.P + x0;
+    ColIO<C> io;
+    io.gin = nullptr;
+    io.gout = a.buf + base;
+    io.cstride = cstride;
+    io.rstride = rstride;
+    io.ccols = min(CT, a.P - x0);
+    io.ncol = min(CT, a.nh - x0);
+    if (MODE == COL_Z_GREEN) {
+      fft_col_fixed<LF, W, CT, false, false, false>(sm, io, tw, tid, NT);
+      col_green<T, CT>(a, sm, nullptr, base, rstride, cstride, x0, outer, io.ncol, L, tid, NT);
+      __syncthreads();
+      fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, NT);
+    } else {
+      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV, false, true>(sm, io, tw, tid, NT);
+    }
+    __syncthreads();
+  }
+  cp_async_wait_all();
+}
+
 }  // namespace hs

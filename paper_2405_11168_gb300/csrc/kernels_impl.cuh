@@ -1,5 +1,7 @@
 // Definitions of the launchers in launch.h; included once per precision.
 #pragma once
+#include <string.h>
+
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -36,13 +38,25 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t smem) {
   return e;
 }
 
-template <typename T, int TY, class MAT, int MODE, bool REAL>
-static cudaError_t march_one(const MarchArgs<T>& a, const MAT& m, dim3 g, int nthr, size_t smem, cudaStream_t s) {
-  auto k = k_march<T, TY, MAT, MODE, REAL>;
+template <typename T, int TY, class MAT, int MODE, bool REAL, bool BATCH>
+static cudaError_t march_launch(const MarchArgs<T>& a, const MAT& m, dim3 g, int nthr, size_t smem,
+                                cudaStream_t s) {
+  auto k = k_march<T, TY, MAT, MODE, REAL, BATCH>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<g, nthr, smem, s>>>(a, m);
   return cudaGetLastError();
+}
+
+// batched launches (zstride != 0) run the real-space force pass only
+template <typename T, int TY, class MAT, int MODE, bool REAL>
+static cudaError_t march_one(const MarchArgs<T>& a, const MAT& m, dim3 g, int nthr, size_t smem, cudaStream_t s) {
+  if constexpr (MODE == MODE_FORCE && REAL) {
+    if (a.zstride != 0) return march_launch<T, TY, MAT, MODE, REAL, true>(a, m, g, nthr, smem, s);
+  } else {
+    if (a.zstride != 0) return cudaErrorInvalidValue;
+  }
+  return march_launch<T, TY, MAT, MODE, REAL, false>(a, m, g, nthr, smem, s);
 }
 
 template <typename T, int TY, bool REAL>
@@ -81,14 +95,26 @@ static cudaError_t march_real(const MarchArgs<T>& a, bool iso, int ty, int mode,
   }
 }
 
-template <int TY, class MATP, int MODE, int N1 = 0>
-static cudaError_t stencil_one(const MarchArgs<float>& a, const MATP& m, dim3 g, int nthr, size_t smem,
-                               cudaStream_t s) {
-  auto k = k_stencil<TY, MATP, MODE, N1>;
+template <int TY, class MATP, int MODE, int N1, bool BATCH>
+static cudaError_t stencil_launch(const MarchArgs<float>& a, const MATP& m, dim3 g, int nthr, size_t smem,
+                                  cudaStream_t s) {
+  auto k = k_stencil<TY, MATP, MODE, N1, BATCH>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<g, nthr, smem, s>>>(a, m);
   return cudaGetLastError();
+}
+
+// batched launches (zstride != 0) run the force pass only
+template <int TY, class MATP, int MODE, int N1 = 0>
+static cudaError_t stencil_one(const MarchArgs<float>& a, const MATP& m, dim3 g, int nthr, size_t smem,
+                               cudaStream_t s) {
+  if constexpr (MODE == MODE_FORCE) {
+    if (a.zstride != 0) return stencil_launch<TY, MATP, MODE, N1, true>(a, m, g, nthr, smem, s);
+  } else {
+    if (a.zstride != 0) return cudaErrorInvalidValue;
+  }
+  return stencil_launch<TY, MATP, MODE, N1, false>(a, m, g, nthr, smem, s);
 }
 
 template <int TY>
@@ -172,13 +198,53 @@ static cudaError_t col_dispatch(const ColArgs<T>& a, int mode, dim3 g, int nthr,
   return col_ct<T, CT>(a, mode, g, nthr, smem, s);
 }
 
-template <typename T, int MODE, int LF = 0>
-static cudaError_t row_one(const RowArgs<T>& a, dim3 nb, int nthr, size_t smem, cudaStream_t s) {
-  auto k = k_row<T, MODE, LF>;
+template <typename T, int CT, int MODE, int LF, int NT>
+static cudaError_t colp_one(const ColArgs<T>& a, dim3 g, size_t smem, cudaStream_t s, int* occ) {
+  auto k = k_colp<T, CT, MODE, LF, NT>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  if (occ != nullptr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, smem);
+  k<<<g, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// the persistent column pass at a fixed length: launch it, or (occ) its blocks per SM
+template <typename T, int CT, int NT, int LF>
+static cudaError_t colp_mode(const ColArgs<T>& a, int mode, dim3 g, size_t smem, cudaStream_t s, int* occ) {
+  switch (mode) {
+    case COL_Y_FWD: return colp_one<T, CT, COL_Y_FWD, LF, NT>(a, g, smem, s, occ);
+    case COL_Y_INV: return colp_one<T, CT, COL_Y_INV, LF, NT>(a, g, smem, s, occ);
+    case COL_Z_GREEN: return colp_one<T, CT, COL_Z_GREEN, LF, NT>(a, g, smem, s, occ);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <typename T, int CT, int NT>
+static cudaError_t colp_dispatch(const ColArgs<T>& a, int mode, int L, dim3 g, int nthr, size_t smem,
+                                 cudaStream_t s, int* occ) {
+  if (nthr != NT) return cudaErrorNotSupported;
+  switch (L) {
+    case 64: return colp_mode<T, CT, NT, 64>(a, mode, g, smem, s, occ);
+    case 128: return colp_mode<T, CT, NT, 128>(a, mode, g, smem, s, occ);
+    case 256: return colp_mode<T, CT, NT, 256>(a, mode, g, smem, s, occ);
+    case 512: return colp_mode<T, CT, NT, 512>(a, mode, g, smem, s, occ);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <typename T, int MODE, int LF, bool BATCH>
+static cudaError_t row_launch(const RowArgs<T>& a, dim3 nb, int nthr, size_t smem, cudaStream_t s) {
+  auto k = k_row<T, MODE, LF, BATCH>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<nb, nthr, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, int MODE, int LF = 0>
+static cudaError_t row_one(const RowArgs<T>& a, dim3 nb, int nthr, size_t smem, cudaStream_t s) {
+  if (a.zstride != 0) return row_launch<T, MODE, LF, true>(a, nb, nthr, smem, s);
+  return row_launch<T, MODE, LF, false>(a, nb, nthr, smem, s);
 }
 
 template <typename T, int MODE, int LF = 0>
@@ -267,6 +333,21 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
     if (ct == (CT)) return col_ct<T, CT>(a, mode, grid, nthr, smem, s);                                  \
     if (ct == (CT) / 2) return col_dispatch<T, (CT) / 2, NT>(a, mode, grid, nthr, smem, s);              \
     return cudaErrorInvalidValue;                                                                        \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_colp<T>(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem,     \
+                             cudaStream_t s) {                                                           \
+    if (a.buf == nullptr || a.tw == nullptr || (mode == COL_Z_GREEN && a.S == nullptr))                  \
+      return cudaErrorInvalidValue;                                                                      \
+    if (ct != (CT) / 2 || plan_ext(a.plan) || a.state_smem) return cudaErrorNotSupported;               \
+    return colp_dispatch<T, (CT) / 2, NT>(a, mode, col_length(a, mode), grid, nthr, smem, s, nullptr);   \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t colp_blocks_per_sm<T>(int mode, int L, int ct, int nthr, size_t smem, int* n) {            \
+    if (ct != (CT) / 2) return cudaErrorNotSupported;                                                    \
+    ColArgs<T> a;                                                                                        \
+    memset(&a, 0, sizeof(a));                                                                            \
+    return colp_dispatch<T, (CT) / 2, NT>(a, mode, L, dim3(1), nthr, smem, nullptr, n);                  \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t launch_row<T>(const RowArgs<T>& a, int mode, dim3 nb, int nthr, size_t smem, cudaStream_t s) { \

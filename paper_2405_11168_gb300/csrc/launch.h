@@ -19,6 +19,14 @@ cudaError_t launch_march(const MarchArgs<T>& a, bool iso, int ty, int mode, bool
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
 
+// persistent double-buffered column pass (COL_Y_FWD, COL_Y_INV, COL_Z_GREEN) for the compile-time
+// lengths 64, 128, 256, 512 with the default tile and block size: grid.x persistent blocks,
+// grid.z items; cudaErrorNotSupported when no such variant exists
+template <typename T>
+cudaError_t launch_colp(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nthr, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t colp_blocks_per_sm(int mode, int L, int ct, int nthr, size_t smem, int* n);
+
 // mode: ROW_C2R / ROW_R2C; grid.x persistent blocks per item, grid.z items (batched launches)
 template <typename T>
 cudaError_t launch_row(const RowArgs<T>& a, int mode, dim3 grid, int nthr, size_t smem, cudaStream_t s);

@@ -342,16 +342,18 @@ __device__ __forceinline__ T march_u(const typename cplx_t<T>::type* ring, const
   return (r & 1) ? z.y : z.x;
 }
 
-template <typename T, int TY, class MAT, int MODE, bool REAL>
+// BATCH: a batched launch (grid.z items, every workspace pointer moved per item); a single
+// solve's launch uses the arguments as they come.
+template <typename T, int TY, class MAT, int MODE, bool REAL, bool BATCH = false>
 __global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a_, const MAT mat_) {
   using C = typename cplx_t<T>::type;
   constexpr int NR = TY + 2;          // corner rows per plane (1 halo row each side)
   constexpr int NSI = 3 * NR / 2;     // packed complex sequences per plane
   constexpr int NSF = 3 * TY / 2;     // packed sequences of the output force
   constexpr int EPC = 16 / (int)sizeof(C);
-  const MarchArgs<T> a = march_item_args(a_);
+  const MarchArgs<T> a = BATCH ? march_item_args(a_) : a_;
   MAT mat = mat_;
-  mat.tab = a.mat;
+  if (BATCH) mat.tab = a.mat;
   if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3, P = a.P, nh = n1 / 2 + 1;

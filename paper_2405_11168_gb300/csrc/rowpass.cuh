@@ -106,10 +106,11 @@ __device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& 
 // LF > 0: N1 = LF and 256 threads per block, fixed at compile time (hot
 // sizes); LF = 0: both taken at run time; LF = -1: run time, plans with a
 // radix-5, 7 or 11 stage.
-template <typename T, int MODE, int LF = 0>
+// BATCH: a batched launch (grid.z items); a single solve's launch uses the arguments as they come.
+template <typename T, int MODE, int LF = 0, bool BATCH = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowArgs<T> a_) {
   using C = typename cplx_t<T>::type;
-  const RowArgs<T> a = row_item_args(a_);
+  const RowArgs<T> a = BATCH ? row_item_args(a_) : a_;
   if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = LF > 0 ? LF : a.n1, P = a.P, nh = n1 / 2 + 1, half = n1 / 2;

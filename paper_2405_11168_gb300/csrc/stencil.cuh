@@ -134,12 +134,14 @@ __device__ __forceinline__ void stencil_prefetch(const MarchArgs<float>& a, cons
 
 // N1 > 0: the x extent is a compile-time constant (hot sizes), so shared
 // memory row offsets become immediates; N1 = 0: taken at run time.
-template <int TY, class MATP, int MODE, int N1 = 0>
+// BATCH: a batched launch (grid.z items, every workspace pointer moved per item);
+// a single solve's launch uses the arguments as they come.
+template <int TY, class MATP, int MODE, int N1 = 0, bool BATCH = false>
 __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a_, const MATP mat_) {
   constexpr int NR = TY + 2;
-  const MarchArgs<float> a = march_item_args(a_);
+  const MarchArgs<float> a = BATCH ? march_item_args(a_) : a_;
   MATP mat = mat_;
-  mat.tab = a.mat;
+  if (BATCH) mat.tab = a.mat;
   if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n1 = N1 > 0 ? N1 : a.n1, n2 = a.n2, n3 = a.n3;

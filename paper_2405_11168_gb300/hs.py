@@ -76,7 +76,8 @@ class hs_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("out_f32", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double), ("zchunk", ctypes.c_int),
                 ("ytile", ctypes.c_int), ("xfuse", ctypes.c_int), ("col_tile", ctypes.c_int),
-                ("col_threads", ctypes.c_int), ("use_graphs", ctypes.c_int), ("col_state", ctypes.c_int)]
+                ("col_threads", ctypes.c_int), ("use_graphs", ctypes.c_int), ("col_state", ctypes.c_int),
+                ("col_pipe", ctypes.c_int)]
 
 
 class HSError(RuntimeError):
