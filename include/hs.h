@@ -105,7 +105,7 @@ typedef struct {
   int col_state;        /* z pass + Green update: 0 = automatic, 1 = state read point by point (L2
                            prefetch), 2 = state tile copied to shared memory during the forward z
                            transform (twice the tile's shared memory); results do not change */
-  int col_pipe;         /* y and z passes at lengths 128, 256, 512 with the default tile: 0 = persistent
+  int col_pipe;         /* y passes at lengths 128, 256, 512 with the default tile: 0 = persistent
                            blocks that copy the next tile while transforming the current one
                            (default), 1 = one tile per block; results do not change */
 } hs_options;

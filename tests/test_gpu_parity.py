@@ -420,7 +420,8 @@ def test_fp64_rigid_surrogate_iterate_by_iterate(hs, contrast):
     """Plain FP64 at contrasts 1e4 and 1e6 (24^3 sphere, the alpha rule) against the oracle, to
     1e-8.  The stiff phase amplifies FP64 rounding by the contrast (the oracle's own floor at 1e6
     is near 1.5e-10), so the two FP64 programs, which sum in different orders, agree on the error
-    history to 1e-4 relative, on the evaluation count to within 2, and on the fields to 1e-8."""
+    history to 1e-4 relative or 2e-10 absolute (measured: up to 5.6e-11 apart at 1e6), on the
+    evaluation count to within 2, and on the fields to 1e-8."""
     ids, table = sphere_case((24, 24, 24), contrast)
     s = hs.Solver(ids, table, precision=hs.HS_FP64)
     out = s.solve(E11, tol=1e-8, max_iter=3000)
@@ -428,7 +429,7 @@ def test_fp64_rigid_surrogate_iterate_by_iterate(hs, contrast):
                        max_iter=3000)
     assert out["status"] == hs.HS_OK and ref.converged and abs(out["iters"] - ref.iters) <= 2
     n = min(out["iters"], ref.iters)
-    np.testing.assert_allclose(s.err_history()[:n], ref.errs[:n], rtol=1e-4, atol=1e-11)
+    np.testing.assert_allclose(s.err_history()[:n], ref.errs[:n], rtol=1e-4, atol=2e-10)
     e_ref, s_ref = voigt_fields(ref)
     assert rel(out["eps"].cpu().numpy(), e_ref) < 1e-8
     assert rel(out["sig"].cpu().numpy(), s_ref) < 1e-8
