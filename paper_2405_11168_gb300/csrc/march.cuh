@@ -181,7 +181,7 @@ __device__ __forceinline__ void tetra_strain_fast(const T (&u)[2][2][2][3], cons
 
 // Shared-memory layout of k_march (host and device use the same function).
 struct MarchLayout {
-  size_t ring, fbuf, stage, ids, src, edge, red, total;
+  size_t ring, fbuf, stage, ids, src, edge, kah, red, total;
   int n1i, n1s;  // row pitches (elements) of the ids and source stages
 };
 
@@ -207,6 +207,9 @@ __host__ __device__ inline MarchLayout march_layout(int n1, int P, int nthr, int
   off += hs_align16(has_src ? (size_t)4 * 2 * 3 * ty * L.n1s : 0);
   L.edge = off;
   off += hs_align16((size_t)tsize * (nthr / 32) * (ty + 1) * 12);
+  // FP32 real-space force pass: per-thread compensated sums (7 values x (sum, compensation))
+  L.kah = off;
+  off += hs_align16((real && tsize == 4 && mode == MODE_FORCE) ? (size_t)4 * 2 * NRED * nthr : 0);
   L.red = off;
   off += 32 * NRED * 8;
   L.total = off;
