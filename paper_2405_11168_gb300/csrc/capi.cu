@@ -1327,9 +1327,13 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       c->grid_m = dim3(yt, nz);
     }
   }
-  // FP64 residual sweep: the widest row tile whose plane ring fits
+  // FP64 residual sweep: the widest row tile whose plane ring fits; 8 rows (1/8 of the rows
+  // recomputed, not 1/4, and no register spills in blocks of at most 256 threads) where N1 <= 256
   c->ty64 = c->ty;
   if (o.precision == HS_FP32_REFINED) {
+    if (o.ytile == 0 && c->n1 <= 256 && c->n2 % 8 == 0 &&
+        march_smem(c->n1, 8, true, hs::MODE_FORCE, true) <= (size_t)smem_optin)
+      c->ty64 = 8;
     while (c->ty64 > 2 && march_smem(c->n1, c->ty64, true, hs::MODE_FORCE, true) > (size_t)smem_optin) c->ty64 /= 2;
     if (c->n2 % c->ty64 != 0) c->ty64 = 2;
   }

@@ -181,7 +181,7 @@ __device__ __forceinline__ void tetra_strain_fast(const T (&u)[2][2][2][3], cons
 
 // Shared-memory layout of k_march (host and device use the same function).
 struct MarchLayout {
-  size_t ring, fbuf, stage, ids, src, edge, kah, red, total;
+  size_t ring, fbuf, stage, ids, src, edge, red, total;
   int n1i, n1s;  // row pitches (elements) of the ids and source stages
 };
 
@@ -207,9 +207,6 @@ __host__ __device__ inline MarchLayout march_layout(int n1, int P, int nthr, int
   off += hs_align16(has_src ? (size_t)4 * 2 * 3 * ty * L.n1s : 0);
   L.edge = off;
   off += hs_align16((size_t)tsize * (nthr / 32) * (ty + 1) * 12);
-  // FP32 real-space force pass: per-thread compensated sums (7 values x (sum, compensation))
-  L.kah = off;
-  off += hs_align16((real && tsize == 4 && mode == MODE_FORCE) ? (size_t)4 * 2 * NRED * nthr : 0);
   L.red = off;
   off += 32 * NRED * 8;
   L.total = off;
@@ -347,8 +344,11 @@ __device__ __forceinline__ T march_u(const typename cplx_t<T>::type* ring, const
 
 // BATCH: a batched launch (grid.z items, every workspace pointer moved per item); a single
 // solve's launch uses the arguments as they come.
+// Blocks of up to 512 threads; the FP64 tile of 8 rows takes blocks of at most 256 (N1 <= 256), so
+// that its registers (up to 255) hold the FP64 sweep without spills.
 template <typename T, int TY, class MAT, int MODE, bool REAL, bool BATCH = false>
-__global__ void __launch_bounds__(512) k_march(const MarchArgs<T> a_, const MAT mat_) {
+__global__ void __launch_bounds__((sizeof(T) == 8 && TY == 8) ? 256 : 512) k_march(const MarchArgs<T> a_,
+                                                                                    const MAT mat_) {
   using C = typename cplx_t<T>::type;
   constexpr int NR = TY + 2;          // corner rows per plane (1 halo row each side)
   constexpr int NSI = 3 * NR / 2;     // packed complex sequences per plane

@@ -18,9 +18,6 @@
 //   its values to the previous warp's lane 31 through shared memory.
 // * The prefetch maps warps to rows and lanes to 16-byte chunks, so the
 //   per-plane copy needs no division.
-// * Sums of sigma^T1 + sigma^T2 and |F|^2 run in FP32 over at most two planes,
-//   then move into per-thread compensated (Kahan) FP32 sums in shared memory;
-//   the block and grid sums are FP64.
 #pragma once
 #include "march.cuh"
 
@@ -175,32 +172,10 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a_, cons
   for (int r = 0; r < TY; ++r)
 #pragma unroll
     for (int k = 0; k < 3; ++k) { Fp[r][k] = 0.f; Fn[r][k] = 0.f; }
-  float2 sacc[6];  // lane x: sum sigma^T1, lane y: sum sigma^T2 (over at most two planes)
+  float2 sacc[6];  // lane x: sum sigma^T1, lane y: sum sigma^T2
 #pragma unroll
   for (int i = 0; i < 6; ++i) sacc[i] = make_float2(0.f, 0.f);
   float facc = 0.f;
-  // every two planes the FP32 partial sums move into this thread's compensated (Kahan) sums,
-  // kept in shared memory: value v at kah[2 v nthr] (sum) and kah[(2 v + 1) nthr] (compensation)
-  if (MODE == MODE_FORCE) {
-    float* kah = reinterpret_cast<float*>(smraw + lay.kah) + tid;
-#pragma unroll
-    for (int v = 0; v < 2 * NRED; ++v) kah[v * nthr] = 0.f;
-  }
-  auto fold = [&]() {
-    float* kah = reinterpret_cast<float*>(smraw + march_layout(n1, 0, nthr, TY, MODE, true, has_src, 4).kah) + tid;
-#pragma unroll
-    for (int v = 0; v < NRED; ++v) {
-      const float x = v < 6 ? sacc[v].x + sacc[v].y : facc;
-      const float sv = kah[2 * v * nthr], cv = kah[(2 * v + 1) * nthr];
-      const float y = x - cv;
-      const float t = sv + y;
-      kah[(2 * v + 1) * nthr] = (t - sv) - y;
-      kah[2 * v * nthr] = t;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sacc[i] = make_float2(0.f, 0.f);
-    facc = 0.f;
-  };
   // 1/2 and -1/2 undo the packing
   const float2 hh = make_float2(0.5f, -0.5f);
   float Em[6];  // engineering macro strain
@@ -403,16 +378,13 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a_, cons
     for (int r = 0; r < TY; ++r)
 #pragma unroll
       for (int k = 0; k < 3; ++k) { Fp[r][k] = Fn[r][k]; Fn[r][k] = 0.f; }
-    if (MODE == MODE_FORCE && (((p - z0) & 1) == 1 || p == pend)) fold();
   }
   cp_async_wait_all();
   if (MODE != MODE_FORCE) return;
   double acc[NRED];
 #pragma unroll
-  for (int v = 0; v < NRED; ++v) {
-    const float* kah = reinterpret_cast<const float*>(smraw + lay.kah) + tid;
-    acc[v] = (double)kah[2 * v * nthr] - (double)kah[(2 * v + 1) * nthr];
-  }
+  for (int i = 0; i < 6; ++i) acc[i] = (double)sacc[i].x + (double)sacc[i].y;
+  acc[6] = (double)facc;
   reduce_and_finalize(acc, a.partials, a.st, a.hist, red);
 }
 
