@@ -378,6 +378,24 @@ def main(argv=None):
             "budget_gb": a.budget_gb, "max_running": srv.max_running, "max_used_gb": srv.max_used / 2**30,
             "contexts_created": srv.created, "contexts_released": srv.released,
             "evaluations": int(sum(sum(r.iters) for r in res)), **latency_stats(res)}
+    # requests whose every solve met the tolerance, and the stream split by grid size
+    ok = [r for r in res if all(st == hs.HS_OK for st in r.status)]
+    if ok:
+        line["converged_requests"] = len(ok)
+        line.update({k + "_converged": v for k, v in latency_stats(ok).items()})
+    size_of = {q.tag: q.ids.shape[0] for q in reqs}
+    by = {}
+    for r in res:
+        d = by.setdefault(str(size_of[r.tag]), {"requests": 0, "solves": 0, "converged": 0, "lat": []})
+        d["requests"] += 1
+        d["solves"] += len(r.status)
+        d["converged"] += sum(int(st == hs.HS_OK) for st in r.status)
+        d["lat"].append(r.latency_s)
+    for d in by.values():
+        lat = d.pop("lat")
+        d["p50_s"] = float(np.percentile(lat, 50))
+        d["p99_s"] = float(np.percentile(lat, 99))
+    line["by_size"] = by
     print(json.dumps(line), flush=True)
     return 0
 
