@@ -15,7 +15,9 @@ divided by the device time of the step (CUDA events, max over ranks).
 Beside the metric the line carries, each from its own leg outside the timed
 region: the iterations and final errors per contrast of the timed solves and the
 oracle's own error at one solve's final state (``err_vs_oracle``); a timing of
-one solve that runs the FP32 correction solves (``correction_solves``); 18
+one solve that runs the FP32 correction solves (``correction_solves``); the
+256^3 microstructure itself solved to 1e-6 at contrasts 1e3, 1e-3 and voids
+(``converged_256``, with the oracle's error at one final state); 18
 solves at 64^3 served to equilibrium error <= 1e-6 in plain FP64 and in FP32 +
 FP64 refinement (``converged``: solves/s, p50/p99, the oracle's error at the
 served states); 64 RVEs of sizes 32^3..128^3 with their 6 load cases in one
@@ -419,6 +421,32 @@ def correction_leg(hs, ids_dev, table, dev, stream):
             "final_err": out["err"], "fp64_sweep_errs": [float(x) for x in hist[40:]][-8:], "kernels": kern}
 
 
+def converged_256_leg(hs, ids, ids_dev, dev, stream):
+    """The bench microstructure itself (256^3) solved to err <= 1e-6 in FP32 + FP64 refinement,
+    E11, one solve per contrast 1e3, 1e-3 and voids (budget 20000 evaluations), timed with CUDA
+    events; the oracle's error at the 1e-3 solve's final state; the rigid surrogate 1e6 with a
+    budget of 2000 evaluations (its FP64 iteration stalls on random packings, see the design notes)."""
+    E = unit_loads()[0]
+    rows = {}
+    for c, budget in ((1e3, 20000), (1e-3, 20000), (0.0, 20000), (1e6, 2000)):
+        table = synth.two_phase_table(1.0, NU, c, NU)
+        s = hs.Solver(ids_dev, table, precision=hs.HS_FP32_REFINED, device=dev, stream=stream)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        o = s.solve(E, tol=TOL, max_iter=budget, fields=False)
+        t1.record(stream)
+        t1.synchronize()
+        row = {"status": o["status"], "converged": o["status"] == hs.HS_OK, "evaluations": o["iters"],
+               "final_err": o["err"], "s": t0.elapsed_time(t1) / 1e3, "budget": budget}
+        if c == 1e-3:
+            row["err_vs_oracle"] = state_check(s, ids, table, E, o["err"], o["sig_eff"])
+        s.close()
+        rows[f"{c:g}"] = row
+    return {"what": f"{GRID[0]}^3 random spheres R=8 f=0.30 seed 1 (the timed workload), E11, FP32 + FP64 "
+                    "refinement, tol 1e-6, one solve per contrast", "solves": rows}
+
+
 CONV_GRID = (64, 64, 64)
 CONV_CONTRASTS = [1e3, 1e-3, 0.0]
 
@@ -778,6 +806,7 @@ def run_ours(args):
                                               "steps 1-4) at the GPU's final displacement")
             s0.close()
         for name, fn in (("correction_solves", lambda: correction_leg(hs, ids_dev, tables[0], dev, stream)),
+                         ("converged_256", lambda: converged_256_leg(hs, ids, ids_dev, dev, stream)),
                          ("converged", lambda: converged_leg(hs, dev)),
                          ("batched", lambda: batched_leg(hs, dev)),
                          ("serving", lambda: serving_leg(hs, dev))):
@@ -849,7 +878,7 @@ def main():
     ap.add_argument("--skip-torch", action="store_true", help="skip the torch.fft comparison pipeline")
     ap.add_argument("--grid", type=int, default=256, help="cubic grid size (profiling runs use smaller cases)")
     ap.add_argument("--ncontrast", type=int, default=4, help="use the first k contrasts (profiling runs)")
-    ap.add_argument("--skip-legs", default="", help="comma-separated legs to skip: correction_solves, converged, "
+    ap.add_argument("--skip-legs", default="", help="comma-separated legs to skip: correction_solves, converged_256, converged, "
                                                     "batched, serving")
     args = ap.parse_args()
     args.skip_legs = [x for x in args.skip_legs.split(",") if x]
