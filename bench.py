@@ -426,6 +426,8 @@ def converged_256_leg(hs, ids, ids_dev, dev, stream):
     E11, one solve per contrast 1e3, 1e-3 and voids (budget 20000 evaluations), timed with CUDA
     events; the oracle's error at the 1e-3 solve's final state; the rigid surrogate 1e6 with a
     budget of 2000 evaluations (its FP64 iteration stalls on random packings, see the design notes)."""
+    import torch
+
     E = unit_loads()[0]
     rows = {}
     for c, budget in ((1e3, 20000), (1e-3, 20000), (0.0, 20000), (1e6, 2000)):

@@ -13,6 +13,7 @@
 #include <tuple>
 #include <type_traits>
 #include <unordered_map>
+#include <functional>
 #include <vector>
 
 #include "../../include/hs.h"
@@ -489,6 +490,37 @@ hs_status check_grid(const int grid[3]) {
 int pitch_of(int nh, bool f64) { return f64 ? ((nh + 1) & ~1) : ((nh + 3) & ~3); }
 
 int pick_ty(int n2) { return (n2 % 4 == 0) ? 4 : 2; }
+
+// z chunk of an FP64 real-space pass.  Its blocks (one per (y tile, z chunk), launched y tile
+// first) are bound by the FP64 pipe, so a block's time is proportional to the voxel layers it
+// computes (chunk + 1) and the pass ends when a greedy list schedule of the blocks, in launch
+// order, on the resident slots ends.  The chunk length with the earliest end is taken (the longer
+// on ties: fewer recomputed layers).  At 256^3 on GB300 this model reproduces the measured
+// sweep times of chunks 8..32 to 1%.
+int pick_zchunk64(int yt, int n3, int slots) {
+  int best_zc = 0;
+  long long best = -1;
+  std::vector<long long> heap(std::max(slots, 1));
+  for (int zc = std::min(4, n3); zc <= std::min(n3, 64); ++zc) {
+    std::fill(heap.begin(), heap.end(), 0LL);
+    long long end = 0;
+    const int nz = (n3 + zc - 1) / zc;
+    for (int z = 0; z < nz; ++z) {
+      const long long layers = std::min(zc, n3 - z * zc) + 1;
+      for (int y = 0; y < yt; ++y) {
+        std::pop_heap(heap.begin(), heap.end(), std::greater<long long>());
+        heap.back() += layers;
+        end = std::max(end, heap.back());
+        std::push_heap(heap.begin(), heap.end(), std::greater<long long>());
+      }
+    }
+    if (best < 0 || end < best || (end == best && zc > best_zc)) {
+      best = end;
+      best_zc = zc;
+    }
+  }
+  return best_zc;
+}
 
 size_t march_smem(int n1, int ty, bool f64, int mode, bool real, bool has_src = false) {
   const int nh = n1 / 2 + 1;
@@ -1327,6 +1359,19 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       c->grid_m = dim3(yt, nz);
     }
   }
+  // FP64 precision: the real-space pass is FP64-bound like the refined mode's sweep
+  if (c->f64 && !c->xfuse && o.zchunk == 0) {
+    int per_sm = 0, nsm = 0;
+    const size_t smf = march_smem(c->n1, c->ty, true, hs::MODE_FORCE, true);
+    if (hs::march_blocks_per_sm<double>(c->iso, c->ty, c->nthr_m, smf, &per_sm) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && per_sm > 0) {
+      const int yt = c->n2 / c->ty;
+      c->zc = pick_zchunk64(yt, c->n3, per_sm * nsm);
+      c->grid_m = dim3(yt, (c->n3 + c->zc - 1) / c->zc);
+    } else {
+      cudaGetLastError();
+    }
+  }
   // FP64 residual sweep: the widest row tile whose plane ring fits; 8 rows (1/8 of the rows
   // recomputed, not 1/4, and no register spills in blocks of at most 256 threads) where N1 <= 256
   c->ty64 = c->ty;
@@ -1341,6 +1386,15 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
     const int yt = c->n2 / c->ty64;
     int nz = std::max(1, std::min(c->n3, (kTargetBlocks + yt - 1) / yt));
     c->zc64 = (c->n3 + nz - 1) / nz;
+    if (o.precision == HS_FP32_REFINED) {
+      int per_sm = 0, nsm = 0;
+      const size_t sm64 = march_smem(c->n1, c->ty64, true, hs::MODE_FORCE, true);
+      if (hs::march_blocks_per_sm<double>(c->iso, c->ty64, c->nthr_m, sm64, &per_sm) == cudaSuccess &&
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && per_sm > 0)
+        c->zc64 = pick_zchunk64(yt, c->n3, per_sm * nsm);
+      else
+        cudaGetLastError();
+    }
     nz = (c->n3 + c->zc64 - 1) / c->zc64;
     c->grid_m64 = dim3(yt, nz);
   }

@@ -84,6 +84,19 @@ static cudaError_t march_ty(const MarchArgs<T>& a, bool iso, int mode, dim3 g, i
   return march_one<T, TY, MatAniso<T>, MODE_FIELDS, REAL>(a, m, g, nthr, smem, s);
 }
 
+// resident blocks per SM of the FP64 real-space force pass (single solves)
+template <int TY, class MAT>
+static cudaError_t march64_occ_one(int nthr, size_t smem, int* n) {
+  auto k = k_march<double, TY, MAT, MODE_FORCE, true, false>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k, nthr, smem);
+}
+template <int TY>
+static cudaError_t march64_occ_ty(bool iso, int nthr, size_t smem, int* n) {
+  return iso ? march64_occ_one<TY, MatIso<double>>(nthr, smem, n) : march64_occ_one<TY, MatAniso<double>>(nthr, smem, n);
+}
+
 template <typename T, bool REAL>
 static cudaError_t march_real(const MarchArgs<T>& a, bool iso, int ty, int mode, dim3 g, int nthr, size_t smem,
                               cudaStream_t s) {
@@ -341,6 +354,16 @@ __global__ void k_state_import(const double2* in, typename cplx_t<T>::type* S, s
       return cudaErrorInvalidValue;                                                                      \
     if (ct != (CT) / 2 || plan_ext(a.plan) || a.state_smem) return cudaErrorNotSupported;               \
     return colp_dispatch<T, (CT) / 2, NT>(a, mode, col_length(a, mode), grid, nthr, smem, s, nullptr);   \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t march_blocks_per_sm<T>(bool iso, int ty, int nthr, size_t smem, int* n) {                 \
+    if (sizeof(T) != 8) return cudaErrorNotSupported;                                                    \
+    switch (ty) {                                                                                        \
+      case 2: return march64_occ_ty<2>(iso, nthr, smem, n);                                              \
+      case 4: return march64_occ_ty<4>(iso, nthr, smem, n);                                              \
+      case 8: return march64_occ_ty<8>(iso, nthr, smem, n);                                              \
+      default: return cudaErrorInvalidValue;                                                             \
+    }                                                                                                    \
   }                                                                                                      \
   template <>                                                                                            \
   cudaError_t colp_blocks_per_sm<T>(int mode, int L, int ct, int nthr, size_t smem, int* n) {            \

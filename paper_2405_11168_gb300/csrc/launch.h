@@ -27,6 +27,10 @@ cudaError_t launch_colp(const ColArgs<T>& a, int mode, int ct, dim3 grid, int nt
 template <typename T>
 cudaError_t colp_blocks_per_sm(int mode, int L, int ct, int nthr, size_t smem, int* n);
 
+// resident blocks per SM of the FP64 real-space force pass of a single solve (T = double only)
+template <typename T>
+cudaError_t march_blocks_per_sm(bool iso, int ty, int nthr, size_t smem, int* n);
+
 // mode: ROW_C2R / ROW_R2C; grid.x persistent blocks per item, grid.z items (batched launches)
 template <typename T>
 cudaError_t launch_row(const RowArgs<T>& a, int mode, dim3 grid, int nthr, size_t smem, cudaStream_t s);
