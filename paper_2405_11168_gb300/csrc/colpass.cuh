@@ -62,6 +62,12 @@ template <typename T> __device__ __forceinline__ ColArgs<T> col_item_args(const 
 }
 
 template <typename T>
+__device__ __forceinline__ void green_core(const ColArgs<T>& a, T c0a, T c0b, bool c0iso,
+                                           typename cplx_t<T>::type yz, typename cplx_t<T>::type xy,
+                                           typename cplx_t<T>::type xz, typename cplx_t<T>::type (&F)[3],
+                                           typename cplx_t<T>::type (&U)[3]);
+
+template <typename T>
 __device__ __forceinline__ void green_apply(const ColArgs<T>& a, T c0a, T c0b, bool c0iso, int h1, int h2, int h3,
                                             typename cplx_t<T>::type (&F)[3],
                                             typename cplx_t<T>::type (&U)[3]) {
@@ -74,7 +80,17 @@ __device__ __forceinline__ void green_apply(const ColArgs<T>& a, T c0a, T c0b, b
     return;
   }
   const C ex = __ldg(a.tw1 + h1), ey = __ldg(a.tw2 + h2), ez = __ldg(a.tw3 + h3);
-  const C yz = cmul(ey, ez), xy = cmul(ex, ey), xz = cmul(ex, ez);
+  green_core<T>(a, c0a, c0b, c0iso, cmul(ey, ez), cmul(ex, ey), cmul(ex, ez), F, U);
+}
+
+// The update at one q from the products of the per-axis phase factors exp(-i q_y) exp(-i q_z)
+// (yz), exp(-i q_x) exp(-i q_y) (xy) and exp(-i q_x) exp(-i q_z) (xz); q not a translation mode.
+template <typename T>
+__device__ __forceinline__ void green_core(const ColArgs<T>& a, T c0a, T c0b, bool c0iso,
+                                           typename cplx_t<T>::type yz, typename cplx_t<T>::type xy,
+                                           typename cplx_t<T>::type xz, typename cplx_t<T>::type (&F)[3],
+                                           typename cplx_t<T>::type (&U)[3]) {
+  using C = typename cplx_t<T>::type;
   const T h = T(0.5);
   // corner-convention symbols (Eq. Dq times exp(-i q.(1/2,1/2,1/2)))
   C D[3];
@@ -176,6 +192,63 @@ __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T
   }
 }
 
+// col_green for a compile-time length L and block size NT (NT a multiple of CT): thread tid keeps
+// column tid % CT and walks z = tid / CT, tid / CT + NT / CT, ..., so exp(-i q_x), its product
+// with the block's exp(-i q_y), the state address of its column and whether its (q_x, q_y) can
+// be a translation mode are set once; per point only exp(-i q_z) and two products remain.
+template <typename T, int CT, int L, int NT>
+__device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cplx_t<T>::type* sm, size_t base,
+                                                size_t rstride, size_t cstride, int x0, int outer, int ncol,
+                                                int tid) {
+  using C = typename cplx_t<T>::type;
+  static_assert(NT % CT == 0 && (L * CT) % NT == 0, "whole columns per thread");
+  constexpr int W = 3 * CT;
+  constexpr int ZS = NT / CT;        // z step of a thread
+  constexpr int NPT = L * CT / NT;   // points per thread
+  constexpr int GU = NPT < 4 ? NPT : 4;
+  const int col = tid % CT, zt = tid / CT;
+  if (col >= ncol) return;
+  const bool c0iso = a.c0iso || a.c0dev != nullptr;
+  const T c0a = a.c0dev != nullptr ? a.c0dev[0] : a.c0a;
+  const T c0b = a.c0dev != nullptr ? a.c0dev[1] : a.c0b;
+  const int h1 = x0 + col, h2 = outer;
+  const C ex = __ldg(a.tw1 + h1), ey = __ldg(a.tw2 + h2);
+  const C xy = cmul(ex, ey);
+  // translation modes q = 0 and (pi, pi, pi): only where (q_x, q_y) is (0, 0) or (pi, pi)
+  const int ztrans = (h1 == 0 && h2 == 0) ? 0 : ((2 * h1 == a.n1 && 2 * h2 == a.n2) ? a.n3 / 2 : -1);
+  C* Sc = a.S + base + col;
+#pragma unroll
+  for (int u0 = 0; u0 < NPT; u0 += GU) {
+    C U[GU][3];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const size_t g = (size_t)(zt + (u0 + u) * ZS) * rstride;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) U[u][c] = Sc[c * cstride + g];
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int z = zt + (u0 + u) * ZS;
+      C F[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[c] = sm[z * W + c * CT + col];
+      if (z == ztrans) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) U[u][c] = cmk<C>(0, 0);
+      } else {
+        const C ez = __ldg(a.tw3 + z);
+        green_core<T>(a, c0a, c0b, c0iso, cmul(ey, ez), xy, cmul(ex, ez), F, U[u]);
+      }
+      const size_t g = (size_t)z * rstride;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Sc[c * cstride + g] = U[u][c];
+        sm[z * W + c * CT + col] = U[u][c];
+      }
+    }
+  }
+}
+
 // LF > 0: the transformed length is LF and the block has NT threads, both
 // fixed at compile time (hot sizes); LF = 0: both taken at run time; LF = -1:
 // run time, plans with a radix-5, 7 or 11 stage.
@@ -256,7 +329,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
         cp_async_wait_all();
         __syncthreads();
       }
-      col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+      if constexpr (NT > 0 && NT % CT == 0 && (LF * CT) % NT == 0) {
+        if (ss == nullptr) col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, ncol, tid);
+        else col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+      } else {
+        col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
+      }
       __syncthreads();
       fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, nthr);
     } else {
