@@ -91,33 +91,34 @@ __device__ __forceinline__ void green_core(const ColArgs<T>& a, T c0a, T c0b, bo
                                            typename cplx_t<T>::type xz, typename cplx_t<T>::type (&F)[3],
                                            typename cplx_t<T>::type (&U)[3]) {
   using C = typename cplx_t<T>::type;
-  const T h = T(0.5);
-  // corner-convention symbols (Eq. Dq times exp(-i q.(1/2,1/2,1/2)))
+  // corner-convention symbols (Eq. Dq times exp(-i q.(1/2,1/2,1/2))), here 2 D
   C D[3];
-  D[0] = cmk<C>(h * (T(1) + yz.x - xy.x - xz.x), h * (yz.y - xy.y - xz.y));
-  D[1] = cmk<C>(h * (T(1) - yz.x - xy.x + xz.x), h * (-yz.y - xy.y + xz.y));
-  D[2] = cmk<C>(h * (T(1) - yz.x + xy.x - xz.x), h * (-yz.y + xy.y - xz.y));
-  // M in Voigt pair order (11,22,33,23,13,12)
+  D[0] = cmk<C>(T(1) + yz.x - xy.x - xz.x, yz.y - xy.y - xz.y);
+  D[1] = cmk<C>(T(1) - yz.x - xy.x + xz.x, -yz.y - xy.y + xz.y);
+  D[2] = cmk<C>(T(1) - yz.x + xy.x - xz.x, -yz.y + xy.y - xz.y);
+  // 2 M in Voigt pair order (11,22,33,23,13,12), M_ik = 2 Re(D_i conj D_k); the factors of two
+  // are powers of two, so folding them into the constants below changes no rounding
   T M[6];
-  M[0] = T(2) * (D[0].x * D[0].x + D[0].y * D[0].y);
-  M[1] = T(2) * (D[1].x * D[1].x + D[1].y * D[1].y);
-  M[2] = T(2) * (D[2].x * D[2].x + D[2].y * D[2].y);
-  M[3] = T(2) * (D[1].x * D[2].x + D[1].y * D[2].y);
-  M[4] = T(2) * (D[0].x * D[2].x + D[0].y * D[2].y);
-  M[5] = T(2) * (D[0].x * D[1].x + D[0].y * D[1].y);
+  M[0] = D[0].x * D[0].x + D[0].y * D[0].y;
+  M[1] = D[1].x * D[1].x + D[1].y * D[1].y;
+  M[2] = D[2].x * D[2].x + D[2].y * D[2].y;
+  M[3] = D[1].x * D[2].x + D[1].y * D[2].y;
+  M[4] = D[0].x * D[2].x + D[0].y * D[2].y;
+  M[5] = D[0].x * D[1].x + D[0].y * D[1].y;
   T A[6];
   if (c0iso) {
     // Omega^-1_jl = sum_ik lambda0_jikl M_ik = (lambda0 + mu0) M_jl + mu0 tr(M) delta_jl
-    const T tr = c0b * (M[0] + M[1] + M[2]);
+    const T tr = (T(0.5) * c0b) * (M[0] + M[1] + M[2]);
+    const T ca = T(0.5) * c0a;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) A[i] = c0a * M[i] + (i < 3 ? tr : T(0));
+    for (int i = 0; i < 6; ++i) A[i] = ca * M[i] + (i < 3 ? tr : T(0));
   } else {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       T s = 0;
 #pragma unroll
       for (int j = 0; j < 6; ++j) s += a.G6[i * 6 + j] * M[j];
-      A[i] = s;
+      A[i] = T(0.5) * s;
     }
   }
   // inverse of the symmetric 3x3 [[A0,A5,A4],[A5,A1,A3],[A4,A3,A2]]

@@ -331,6 +331,16 @@ template <int ES, int PS> __host__ __device__ __forceinline__ int seq_pos(int e)
 }
 __host__ __device__ __forceinline__ int rswz(int e) { return seq_pos<1, -2>(e); }
 
+// The row swizzle is linear over XOR (shifts, XOR and masks are), and an index that is a sum of
+// parts with disjoint bits is their XOR, so swz(a + b) = swz(a) ^ swz(b) for such parts: a
+// thread swizzles its own offset once per stage and each element adds one XOR with a constant.
+__host__ __device__ constexpr int swz_c(int e) { return e ^ (((e >> 2) ^ (e >> 3)) & 15); }
+__host__ __device__ constexpr int ilog2_c(int v) { return v <= 1 ? 0 : 1 + ilog2_c(v >> 1); }
+// b = pq NS + kk (kk < NS) -> pq NS R + kk: the bits of b at and above log2 NS move up by log2 R
+template <int NS, int R> __device__ __forceinline__ int stockham_out(int b) {
+  return ((b >> ilog2_c(NS)) << (ilog2_c(NS) + ilog2_c(R))) | (b & (NS - 1));
+}
+
 // one stage; sequence s element e at buf[s*SS + seq_pos<ES, PS>(e)]
 template <int L, int R, int NS, int SS, int ES, int PS, bool INV, typename C>
 __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, const C* __restrict__ tw, bool wsync) {
@@ -338,6 +348,12 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
   constexpr int nb = L / R;
   constexpr int KB = (nb + T - 1) / T;
   constexpr int step = L / (NS * R);
+  // swizzled rows (PS = -2): T, nb, NS and R are powers of two and t < T, so the loads' index
+  // b + m nb = t + k T + m nb and the stores' pq NS R + kk + m NS split into disjoint parts
+  constexpr bool XS = (PS == -2) && (T & (T - 1)) == 0 && (nb & (nb - 1)) == 0 && (NS & (NS - 1)) == 0 &&
+                      (R & (R - 1)) == 0;
+  const int tin = XS ? swz_c(t) : 0;
+  const int tout = XS ? swz_c(stockham_out<NS, R>(t)) : 0;
   C v[KB][R];
   C* sb = buf + s * SS;
 #pragma unroll
@@ -347,7 +363,8 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int e = b + m * nb;
-        v[k][m] = sb[seq_pos<ES, PS>(e)];
+        if constexpr (XS) v[k][m] = sb[tin ^ swz_c(k * T + m * nb)];
+        else v[k][m] = sb[seq_pos<ES, PS>(e)];
       }
     }
   }
@@ -371,7 +388,8 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int e = base + m * NS;
-        sb[seq_pos<ES, PS>(e)] = v[k][m];
+        if constexpr (XS) sb[tout ^ swz_c(stockham_out<NS, R>(k * T) + m * NS)] = v[k][m];
+        else sb[seq_pos<ES, PS>(e)] = v[k][m];
       }
     }
   }

@@ -127,6 +127,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
   const int pitch = LF > 0 ? FP : rpitch(n1);
   C* z = reinterpret_cast<C*>(smraw) + (size_t)grp * pitch;
   auto zi = [](int e) { return LF > 0 ? rswz(e) : rpad(e); };
+  // fixed lengths: the positions of elements t + j T8 and n1 - (t + j T8) from the thread's
+  // swizzled offsets and one XOR with a constant (the swizzle is linear over XOR; see fft.cuh)
+  constexpr int T8C = LF > 0 ? LF / kE : 1;
+  const int tsw = LF > 0 ? rswz(t) : 0;
+  const int tmir = (LF > 0 && t > 0) ? rswz(T8C - t) : 0;
+  auto zfwd = [&](int j) { return LF > 0 ? (tsw ^ swz_c(j * T8C)) : zi(t + j * T8); };
+  auto zmir = [&](int j) {  // position of n1 - (t + j T8), for t + j T8 > 0
+    if (LF > 0) return t == 0 ? swz_c(LF - j * T8C) : (tmir ^ swz_c(LF - (j + 1) * T8C));
+    return zi(n1 - t - j * T8);
+  };
   const int nseq = a.nrows / 2;
   const int nbatch = (nseq + G - 1) / G;
   const FftPlan plan = a.plan;
@@ -151,13 +161,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
         const C* A = reinterpret_cast<const C*>(stg + (size_t)(2 * grp) * L.rowbytes);
         const C* B = reinterpret_cast<const C*>(stg + (size_t)(2 * grp + 1) * L.rowbytes);
         // Z[k] and its mirror Z[N1-k] from one read of A[k], B[k]
+        if constexpr (LF > 0) {
+#pragma unroll
+          for (int j = 0; j <= LF / 2 / T8C; ++j) {
+            const int k = t + j * T8C;
+            if (k <= half) {
+              C va = A[k], vb = B[k];
+              const bool edge = (k == 0 || k == half);
+              if (edge) { va.y = 0; vb.y = 0; }
+              z[zfwd(j)] = cmk<C>(va.x - vb.y, va.y + vb.x);
+              if (!edge) z[zmir(j)] = cmk<C>(va.x + vb.y, vb.x - va.y);
+            }
+          }
+        } else {
 #pragma unroll 2
-        for (int k = t; k <= half; k += T8) {
-          C va = A[k], vb = B[k];
-          const bool edge = (k == 0 || k == half);
-          if (edge) { va.y = 0; vb.y = 0; }
-          z[zi(k)] = cmk<C>(va.x - vb.y, va.y + vb.x);
-          if (!edge) z[zi(n1 - k)] = cmk<C>(va.x + vb.y, vb.x - va.y);
+          for (int k = t; k <= half; k += T8) {
+            C va = A[k], vb = B[k];
+            const bool edge = (k == 0 || k == half);
+            if (edge) { va.y = 0; vb.y = 0; }
+            z[zi(k)] = cmk<C>(va.x - vb.y, va.y + vb.x);
+            if (!edge) z[zi(n1 - k)] = cmk<C>(va.x + vb.y, vb.x - va.y);
+          }
         }
       }
       group_sync(wsync);
@@ -171,10 +195,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
         __syncthreads();  // every group is done with the staged input
         if (act) {
           T* o = reinterpret_cast<T*>(stg) + (size_t)(2 * grp) * n1;
-          for (int x = t; x < n1; x += T8) {
-            const C w = z[zi(x)];
-            o[x] = w.x;
-            o[n1 + x] = w.y;
+          if constexpr (LF > 0) {
+#pragma unroll
+            for (int j = 0; j < LF / T8C; ++j) {
+              const C w = z[zfwd(j)];
+              o[t + j * T8C] = w.x;
+              o[n1 + t + j * T8C] = w.y;
+            }
+          } else {
+            for (int x = t; x < n1; x += T8) {
+              const C w = z[zi(x)];
+              o[x] = w.x;
+              o[n1 + x] = w.y;
+            }
           }
         }
         fence_async_smem();
@@ -203,12 +236,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       if (act) {
         const T* ra = reinterpret_cast<const T*>(stg + (size_t)(2 * grp) * L.rowbytes);
         const T* rb = reinterpret_cast<const T*>(stg + (size_t)(2 * grp + 1) * L.rowbytes);
+        if constexpr (LF > 0) {
+#pragma unroll
+          for (int j = 0; j < LF / T8C; ++j) {
+            C w;
+            w.x = ra[t + j * T8C];
+            w.y = rb[t + j * T8C];
+            z[zfwd(j)] = w;
+          }
+        } else {
 #pragma unroll 4
-        for (int x = t; x < n1; x += T8) {
-          C w;
-          w.x = ra[x];
-          w.y = rb[x];
-          z[zi(x)] = w;
+          for (int x = t; x < n1; x += T8) {
+            C w;
+            w.x = ra[x];
+            w.y = rb[x];
+            z[zi(x)] = w;
+          }
         }
       }
       group_sync(wsync);
@@ -247,9 +290,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       if (act) {
         C* A = a.spec_out + r0 * P;
         C* B = a.spec_out + r1 * P;
-        for (int k = t; k < nh; k += T8) {
-          const C zk = z[zi(k)];
-          const C zn = z[zi(k == 0 ? 0 : n1 - k)];
+        // A[k], B[k] from Z[k] and Z[N1-k] (k = 0: Z[0] twice)
+        auto separate = [&](int k, const C zk, const C zn) {
           C va, vb;
           va.x = T(0.5) * (zk.x + zn.x);
           va.y = T(0.5) * (zk.y - zn.y);
@@ -257,6 +299,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
           vb.y = T(0.5) * (zn.x - zk.x);
           A[k] = va;
           B[k] = vb;
+        };
+        if constexpr (LF > 0) {
+#pragma unroll
+          for (int j = 0; j <= LF / 2 / T8C; ++j) {
+            const int k = t + j * T8C;
+            if (k < nh) separate(k, z[zfwd(j)], z[k == 0 ? 0 : zmir(j)]);
+          }
+        } else {
+          for (int k = t; k < nh; k += T8) separate(k, z[zi(k)], z[zi(k == 0 ? 0 : n1 - k)]);
         }
       }
     }
