@@ -45,7 +45,7 @@ typedef enum {
   HS_ERR_OOM = -3,             /* the workspace given is smaller than hs_workspace_size() */
   HS_ERR_CUDA = -4,            /* a CUDA call failed (see hs_last_error) */
   HS_DIVERGED = -5,            /* err became NaN/Inf or grew 1e6x above its minimum */
-  HS_ERR_TIMEOUT = -6          /* reserved: a bounded device wait gave up */
+  HS_ERR_TIMEOUT = -6          /* a bounded device wait (a tensor copy's barrier) gave up */
 } hs_status;
 
 enum { HS_FP64 = 0, HS_FP32 = 1, HS_FP32_REFINED = 2 };
@@ -108,6 +108,12 @@ typedef struct {
   int col_pipe;         /* y passes at lengths 128, 256, 512 with the default tile: 0 = persistent
                            blocks that copy the next tile while transforming the current one
                            (default), 1 = one tile per block; results do not change */
+  int col_copy;         /* tile loads of the persistent y passes (y lengths 128, 256, 512): 0 = tensor
+                           (TMA) copies where the driver encodes the tile map, else 16-byte cp.async
+                           (default); 1 = cp.async; 2 = as 0, but HS_ERR_UNSUPPORTED_SIZE where a
+                           persistent y pass cannot have its map; results do not change.  A tensor
+                           copy that does not complete within a bounded wait ends the solve with
+                           HS_ERR_TIMEOUT */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,

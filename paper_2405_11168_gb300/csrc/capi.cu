@@ -16,6 +16,9 @@
 #include <functional>
 #include <vector>
 
+#include <cuda.h>  // tensor-map types; the encoder is fetched through the runtime
+#include <cudaTypedefs.h>
+
 #include "../../include/hs.h"
 #include "launch.h"
 
@@ -253,6 +256,13 @@ struct hs_ctx {
   bool zstate_smem = false;  // the z pass copies the state tile to shared memory
   // persistent double-buffered y / z passes (k_colp): blocks and shared memory
   bool pipe_y = false, pipe_z = false;
+  // persistent y passes fed by tensor copies: the map of work buffer B[b], cached with the
+  // base, item stride and item count it was made for
+  CUtensorMap ymap[2];
+  const void* ymap_base[2] = {nullptr, nullptr};
+  size_t ymap_stride[2] = {0, 0};
+  int ymap_n[2] = {0, 0};
+  bool ymap_ok[2] = {false, false};
   int nblk_py = 0, nblk_pz = 0;
   size_t smem_py = 0, smem_pz = 0;
   dim3 grid_y, grid_z;
@@ -689,10 +699,70 @@ template <typename T> hs_status launch_stencil(hs_ctx* c, const double E[6], con
   return HS_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime (null if unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The tensor map of the y-pass tiles of B[b] (see ColArgs::tmap): T elements of the half
+// spectrum as (2P x-values, 3 components, n2, n3, items) with the components' stride inside y,
+// box (2 ct, 3, min(n2, 256), 1, 1).  Made once per buffer, base and batch shape.  False when
+// the driver offers no encoder or refuses the map; the caller then copies with cp.async.
+bool ymap_for(hs_ctx* c, int b, CUtensorMap* out) {
+  const void* base = c->B[b];
+  const int n = std::max(1, c->batch_n);
+  if (c->ymap_base[b] != base || c->ymap_stride[b] != c->batch_stride || c->ymap_n[b] != n) {
+    c->ymap_base[b] = base;
+    c->ymap_stride[b] = c->batch_stride;
+    c->ymap_n[b] = n;
+    c->ymap_ok[b] = false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    const size_t cs = c->f64 ? 16 : 8;
+    const size_t row = (size_t)c->P * cs, plane = row * c->n2, comp = plane * c->n3;
+    const cuuint64_t dims[5] = {(cuuint64_t)2 * c->P, 3, (cuuint64_t)c->n2, (cuuint64_t)c->n3, (cuuint64_t)n};
+    const cuuint64_t strides[4] = {comp, row, plane, c->batch_stride != 0 ? c->batch_stride : 3 * comp};
+    const cuuint32_t box[5] = {(cuuint32_t)(2 * c->ct), 3, (cuuint32_t)std::min(c->n2, 256), 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const bool aligned = ((uintptr_t)base % 16 == 0) && (2 * c->ct * (cs / 2)) % 16 == 0 && row % 16 == 0 &&
+                         (c->batch_stride % 16 == 0) && (c->n2 <= 256 || c->n2 % 256 == 0);
+    if (enc != nullptr && aligned &&
+        enc(&c->ymap[b], c->f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5,
+            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      c->ymap_ok[b] = true;
+  }
+  if (c->ymap_ok[b]) *out = c->ymap[b];
+  return c->ymap_ok[b];
+}
+
+// ColArgs of a persistent y pass over B[b]: tensor copies where the option and the map allow
+template <typename T> hs_status set_ymap(hs_ctx* c, hs::ColArgs<T>& a, int b) {
+  a.tma = 0;
+  if (!c->pipe_y || c->opt.col_copy == 1) return HS_OK;
+  if (ymap_for(c, b, &a.tmap)) {
+    a.tma = 1;
+    return HS_OK;
+  }
+  if (c->opt.col_copy == 2) return fail(c, HS_ERR_UNSUPPORTED_SIZE, "tensor copies unavailable for the y passes");
+  return HS_OK;
+}
+
 template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   hs::ColArgs<T> a;
   cudaError_t e;
   fill_col<T>(c, a, c->B[buf], 1);
+  if (hs_status st = set_ymap<T>(c, a, buf); st != HS_OK) return st;
   {
     LaunchScope ls(c, HS_K_YFWD);
     e = c->pipe_y ? hs::launch_colp<T>(a, hs::COL_Y_FWD, c->ct, zg(c, dim3(c->nblk_py)), c->nthr_y, c->smem_py, c->stream)
@@ -708,6 +778,7 @@ template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z green)");
   fill_col<T>(c, a, c->B[buf], 1);
+  if (hs_status st = set_ymap<T>(c, a, buf); st != HS_OK) return st;
   {
     LaunchScope ls(c, HS_K_YINV);
     e = c->pipe_y ? hs::launch_colp<T>(a, hs::COL_Y_INV, c->ct, zg(c, dim3(c->nblk_py)), c->nthr_y, c->smem_py, c->stream)
@@ -871,6 +942,8 @@ hs_status iterate(hs_ctx* c, const double E[6], const float* src, DevStatus* hst
 }
 
 hs_status status_code(const DevStatus& h) {
+  if (h.done == hs::DONE_TIMEOUT) return HS_ERR_TIMEOUT;
+  if (h.done == hs::DONE_FAULT) return HS_ERR_CUDA;
   if (h.done == hs::DONE_CONVERGED) return HS_OK;
   if (h.done == hs::DONE_DIVERGED) return HS_DIVERGED;
   return HS_NOT_CONVERGED;
@@ -993,6 +1066,8 @@ hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter,
       if (n) HS_CU(c, cudaMemcpy(h32.data(), c->hist, n * sizeof(double), cudaMemcpyDeviceToHost));
       c->hist_host.insert(c->hist_host.end(), h32.begin(), h32.end());
     }
+    if (hin.done == hs::DONE_TIMEOUT) return fail(c, HS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (hin.done == hs::DONE_FAULT) return fail(c, HS_ERR_CUDA, "a kernel's alignment check failed");
     if (hin.done == hs::DONE_DIVERGED) {
       HS_CU(c, cudaStreamSynchronize(c->stream));
       for (int i = 0; i < 6; ++i) sig_eff[i] = hin.sig_mean[i];
@@ -1048,6 +1123,8 @@ hs_status solve_refined(hs_ctx* c, const double E0[6], double tol, int max_iter,
     s = iterate<float>(c, zeroE, c->rsrc, &hin, &last_in);
     if (s != HS_OK) return s;
     total += hin.evals;
+    if (hin.done == hs::DONE_TIMEOUT) return fail(c, HS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (hin.done == hs::DONE_FAULT) return fail(c, HS_ERR_CUDA, "a kernel's alignment check failed");
     if (hin.done == hs::DONE_DIVERGED) { result = HS_DIVERGED; break; }
     // u64 += du, du = inverse transform of the correction state
     s = launch_state_to_buf<float>(c, 0);
@@ -1114,6 +1191,7 @@ hs_status hs_default_options(hs_options* opt) {
   opt->use_graphs = 1;
   opt->col_state = 0;
   opt->col_pipe = 0;
+  opt->col_copy = 0;
   return HS_OK;
 }
 
@@ -1159,7 +1237,7 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
       (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0 ||
       (o.use_graphs != 0 && o.use_graphs != 1) || o.col_state < 0 || o.col_state > 2 ||
-      (o.col_pipe != 0 && o.col_pipe != 1))
+      (o.col_pipe != 0 && o.col_pipe != 1) || o.col_copy < 0 || o.col_copy > 2)
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > HS_MAX_PHASES)
@@ -1444,7 +1522,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
     for (int axis = 1; axis <= 1 && o.col_pipe == 0 && !ext && nsm > 0; ++axis) {
       const int L = c->n2;
       if (L != 128 && L != 256 && L != 512) continue;
-      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs;
+      // the y passes may load their tiles by tensor copies: room for their alignment and barriers
+      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + (axis == 1 ? hs::kColpTmaSlack : 0);
       if (smem > (size_t)smem_optin) continue;
       const int nthr = axis == 1 ? c->nthr_y : c->nthr_z;
       int per_sm = 0;

@@ -16,11 +16,16 @@
 // equilibrium residual f of Eq. basic_scheme_dep_2); 1/N is the forward
 // normalisation of Eq. FT, applied here once.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the descriptor type only; no driver call from device code)
+
 #include "common.cuh"
 
 namespace hs {
 
 enum { COL_Y_FWD = 0, COL_Y_INV = 1, COL_Z_GREEN = 2, COL_Z_INV_STATE = 3 };
+// dynamic shared memory a TMA-fed persistent column pass needs beyond its two tiles (alignment
+// of the tiles to 128 bytes, two mbarriers)
+constexpr size_t kColpTmaSlack = 256;
 
 template <typename T> struct ColArgs {
   using C = typename cplx_t<T>::type;
@@ -39,11 +44,16 @@ template <typename T> struct ColArgs {
   int c0iso;
   T c0a, c0b;
   const T* c0dev;    // not null: (c0a, c0b) read here (per item in batched launches)
-  const DevStatus* st;
+  DevStatus* st;
   int skip_if_done;
   size_t zstride;    // batched launches: bytes between the workspaces of consecutive items
   int state_smem;    // COL_Z_GREEN: 1 = the state tile is copied to shared memory beside the force
                      // tile (its copy overlaps the forward transform); 0 = read point by point
+  int tma;           // persistent y passes: tiles loaded by tensor copies described by tmap
+  // rank-5 tiled map of buf as T elements: (2P x-values, 3 components, n2, n3, items), box
+  // (2 CT, 3, min(n2, 256), 1, 1); the component dimension sits inside y so that a box lands
+  // as the [e][comp][col] tile
+  CUtensorMap tmap;
 };
 
 template <typename T> __device__ __forceinline__ ColArgs<T> col_item_args(const ColArgs<T>& a) {
@@ -369,19 +379,34 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
 // and copies the next tile into its second buffer while it transforms the current
 // one, so the copies overlap the arithmetic.  Y_FWD, Y_INV and Z_GREEN (state read
 // point by point after an L2 prefetch issued with the tile's copy).
-template <typename T, int CT, int MODE, int LF, int NT>
-__global__ void __launch_bounds__(NT, 2) k_colp(const ColArgs<T> a_) {
+// TMA (y passes): thread 0 issues each tile as tensor copies (one per 256 rows) completing on the
+// tile buffer's mbarrier, every thread waits on it (bounded; a timeout is recorded in the status).
+template <typename T, int CT, int MODE, int LF, int NT, bool TMA = false>
+__global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<T> a_) {
   using C = typename cplx_t<T>::type;
   static_assert(LF > 0 && MODE != COL_Z_INV_STATE, "persistent column pass: fixed lengths, iteration modes");
+  static_assert(!TMA || MODE == COL_Y_FWD || MODE == COL_Y_INV, "tensor copies: y passes");
   const ColArgs<T> a = col_item_args(a_);
   if (a.st->retired || (a.skip_if_done && a.st->done)) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   constexpr bool yaxis = (MODE == COL_Y_FWD || MODE == COL_Y_INV);
   constexpr int L = LF, W = 3 * CT;
   constexpr int EPC = 16 / (int)sizeof(C);
   constexpr int CPR = CT / EPC;
-  C* const sm0 = reinterpret_cast<C*>(smraw);  // [2][L][3][CT]
+  // TMA: the tiles start on a 128-byte boundary (tensor copy destinations), the two barriers
+  // follow them; the host adds kColpTmaSlack bytes to the dynamic shared memory for this
+  unsigned char* const smb = TMA ? smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u) : smraw;
+  C* const sm0 = reinterpret_cast<C*>(smb);  // [2][L][3][CT]
+  uint64_t* const tbar = reinterpret_cast<uint64_t*>(smb + (size_t)2 * L * W * sizeof(C));
   const int tid = threadIdx.x;
+  if (TMA) {
+    // the copy needs a 128-byte aligned destination and a 64-byte aligned map: checked once,
+    // the pass ends with an error status instead of issuing a misaligned copy
+    if ((smem_u32(sm0) & 127u) != 0 || (reinterpret_cast<uintptr_t>(&a_.tmap) & 63u) != 0) {
+      if (tid == 0) a.st->done = DONE_FAULT;
+      return;
+    }
+  }
   const size_t plane = (size_t)a.n2 * a.P;
   const size_t cstride = (size_t)a.n3 * plane;
   const size_t rstride = yaxis ? (size_t)a.P : plane;
@@ -409,15 +434,40 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const ColArgs<T> a_) {
       }
     }
   };
+  // tile t into buffer b by tensor copies (thread 0)
+  auto load_tma = [&](int t, int b) {
+    const int x0 = (t % xtiles) * CT, outer = t / xtiles;
+    C* sm = sm0 + (size_t)b * L * W;
+    mbar_arrive_expect_tx(&tbar[b], (unsigned)(L * W * sizeof(C)));
+#pragma unroll
+    for (int h = 0; h < (L + 255) / 256; ++h)
+      tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, h * 256, outer, (int)blockIdx.z, &tbar[b]);
+  };
+  bool timed_out = false;
   int t = blockIdx.x;
-  if (t < ntiles) load(t, sm0);
-  cp_async_commit();
+  if constexpr (TMA) {
+    if (tid == 0) {
+      mbar_init(&tbar[0], 1);
+      mbar_init(&tbar[1], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0 && t < ntiles) load_tma(t, 0);
+  } else {
+    if (t < ntiles) load(t, sm0);
+    cp_async_commit();
+  }
   for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
     C* sm = sm0 + (size_t)(k & 1) * L * W;
     // the other buffer was freed by the barrier that ended the previous tile
-    if (t + (int)gridDim.x < ntiles) load(t + gridDim.x, sm0 + (size_t)((k + 1) & 1) * L * W);
-    cp_async_commit();
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    if constexpr (TMA) {
+      if (tid == 0 && t + (int)gridDim.x < ntiles) load_tma(t + gridDim.x, (k + 1) & 1);
+      timed_out |= !mbar_wait(&tbar[k & 1], (unsigned)((k >> 1) & 1));
+    } else {
+      if (t + (int)gridDim.x < ntiles) load(t + gridDim.x, sm0 + (size_t)((k + 1) & 1) * L * W);
+      cp_async_commit();
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    }
     __syncthreads();
     const int x0 = (t % xtiles) * CT, outer = t / xtiles;
     const size_t base = yaxis ? (size_t)outer * plane + x0 : (size_t)outer * a.P + x0;
@@ -436,9 +486,12 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const ColArgs<T> a_) {
     } else {
       fft_col_fixed<LF, W, CT, MODE == COL_Y_INV, false, true>(sm, io, tw, tid, NT);
     }
+    // this tile's shared writes come before the tensor copy that refills the buffer
+    if (TMA) fence_async_smem();
     __syncthreads();
   }
   cp_async_wait_all();
+  if (TMA && timed_out) a.st->done = DONE_TIMEOUT;
 }
 
 }  // namespace hs

@@ -38,7 +38,9 @@ struct DevStatus {
   double err_first;
 };
 
-enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
+// DONE_TIMEOUT: a bounded device wait (the mbarrier of a tensor copy) gave up; DONE_FAULT: a
+// kernel's own check (the alignment a tensor copy needs) failed before the access.  Both stay set.
+enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3, DONE_TIMEOUT = 4, DONE_FAULT = 5 };
 
 // Batched launches (one launch over many solves of the same grid): item
 // blockIdx.z works in the workspace that starts zstride bytes after item
@@ -99,6 +101,10 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 // done flag, applied-stress strain update) and clears the arrival counter.
 // One thread calls it.
 __device__ inline void finalize_eval(DevStatus* st, double* hist, const double* sums) {
+  if (st->done == DONE_TIMEOUT || st->done == DONE_FAULT) {
+    st->counter = 0;
+    return;
+  }
   const double n = st->nvox;
   double sm[6], nrm2 = 0;
 #pragma unroll
@@ -199,6 +205,49 @@ __device__ inline void reduce_and_finalize(const double (&acc)[NRED], double* pa
   }
   __syncthreads();
   if (tid == 0) finalize_eval(st, hist, scratch);
+}
+
+// ---- mbarriers and tensor (TMA) copies ------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the initialised barriers visible to the async proxy (then a block barrier)
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Wait for the completion of the barrier phase of the given parity, at most about 2^22 tries
+// (each try may suspend the thread for a while); false if the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t b = smem_u32(bar);
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// Tiled tensor copy global -> shared of the box at coordinates (c0 .. c4) of a rank-5 tensor map
+// (a __grid_constant__ kernel parameter), completing on the mbarrier.  The innermost coordinate
+// times the element size must be a multiple of 16 bytes; dst 128-byte aligned.
+__device__ __forceinline__ void tma_load_5d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
 }
 
 }  // namespace hs

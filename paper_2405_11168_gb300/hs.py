@@ -77,7 +77,7 @@ class hs_options(ctypes.Structure):
                 ("inner_max", ctypes.c_int), ("inner_ratio", ctypes.c_double), ("zchunk", ctypes.c_int),
                 ("ytile", ctypes.c_int), ("xfuse", ctypes.c_int), ("col_tile", ctypes.c_int),
                 ("col_threads", ctypes.c_int), ("use_graphs", ctypes.c_int), ("col_state", ctypes.c_int),
-                ("col_pipe", ctypes.c_int)]
+                ("col_pipe", ctypes.c_int), ("col_copy", ctypes.c_int)]
 
 
 class HSError(RuntimeError):

@@ -250,6 +250,28 @@ def test_deterministic_repeat(hs):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("grid", [(40, 128, 12), (24, 256, 6), (20, 512, 6)])
+def test_y_pass_tensor_copies_match_cp_async(hs, prec, grid):
+    """The persistent y passes' tiles loaded by tensor (TMA) copies give bit-identical
+    iterates, fields and errors to the 16-byte cp.async loads, in FP64, FP32 and refined mode,
+    on y lengths 128, 256 and 512 (two copies per tile) with ragged x tiles (the last tile of 8
+    or 4 columns partly past the row pitch, filled with zeros by the copy)."""
+    ids = synth.random_phase_map(tuple(grid), 2, seed=7)
+    table = synth.two_phase_table(1.0, 0.3, 6.0, 0.3)
+    runs = []
+    for copy in (1, 2):
+        s = hs.Solver(ids, table, precision=prec, col_copy=copy, inner_max=8)
+        out = s.solve(E_MIX, tol=1e-9, max_iter=30)
+        runs.append((out["iters"], out["err"], out["sig_eff"].copy(), out["eps"].cpu().numpy(),
+                     out["sig"].cpu().numpy(), s.err_history().copy()))
+        s.close()
+    a, b = runs
+    assert a[0] == b[0] and a[1] == b[1]
+    for i in (2, 3, 4, 5):
+        np.testing.assert_array_equal(a[i], b[i])
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_graph_replay_matches_plain_launches(hs, prec):
     """Iteration chunks replayed as captured CUDA graphs give bit-identical iterates,
     fields and errors to plain launches, across solves with different loads and after
