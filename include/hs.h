@@ -108,12 +108,12 @@ typedef struct {
   int col_pipe;         /* y passes at lengths 128, 256, 512 with the default tile: 0 = persistent
                            blocks that copy the next tile while transforming the current one
                            (default), 1 = one tile per block; results do not change */
-  int col_copy;         /* tile loads of the persistent y passes (y lengths 128, 256, 512): 0 = tensor
+  int col_copy;         /* tile loads of the persistent y passes (y lengths 128, 256, 512) and of the
+                           z pass (z lengths 64, 128, 256, 512, state read point by point): 0 = tensor
                            (TMA) copies where the driver encodes the tile map, else 16-byte cp.async
-                           (default); 1 = cp.async; 2 = as 0, but HS_ERR_UNSUPPORTED_SIZE where a
-                           persistent y pass cannot have its map; results do not change.  A tensor
-                           copy that does not complete within a bounded wait ends the solve with
-                           HS_ERR_TIMEOUT */
+                           (default); 1 = cp.async; 2 = as 0, but HS_ERR_UNSUPPORTED_SIZE where such a
+                           pass cannot have its map; results do not change.  A tensor copy that does
+                           not complete within a bounded wait ends the solve with HS_ERR_TIMEOUT */
 } hs_options;
 
 /* Fill *opt with defaults: FP64, check_every 8, double outputs,

@@ -256,13 +256,13 @@ struct hs_ctx {
   bool zstate_smem = false;  // the z pass copies the state tile to shared memory
   // persistent double-buffered y / z passes (k_colp): blocks and shared memory
   bool pipe_y = false, pipe_z = false;
-  // persistent y passes fed by tensor copies: the map of work buffer B[b], cached with the
-  // base, item stride and item count it was made for
-  CUtensorMap ymap[2];
-  const void* ymap_base[2] = {nullptr, nullptr};
-  size_t ymap_stride[2] = {0, 0};
-  int ymap_n[2] = {0, 0};
-  bool ymap_ok[2] = {false, false};
+  // column passes fed by tensor copies: the tile map of work buffer B[b] for the y (axis 0)
+  // and z (axis 1) passes, cached with the base, item stride and item count it was made for
+  CUtensorMap tmap[2][2];
+  const void* tmap_base[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  size_t tmap_stride[2][2] = {{0, 0}, {0, 0}};
+  int tmap_n[2][2] = {{0, 0}, {0, 0}};
+  bool tmap_ok[2][2] = {{false, false}, {false, false}};
   int nblk_py = 0, nblk_pz = 0;
   size_t smem_py = 0, smem_pz = 0;
   dim3 grid_y, grid_z;
@@ -714,47 +714,53 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   return fn;
 }
 
-// The tensor map of the y-pass tiles of B[b] (see ColArgs::tmap): T elements of the half
+// The tensor map of the column-pass tiles of B[b] (see ColArgs::tmap): T elements of the half
 // spectrum as (2P x-values, 3 components, n2, n3, items) with the components' stride inside y,
-// box (2 ct, 3, min(n2, 256), 1, 1).  Made once per buffer, base and batch shape.  False when
-// the driver offers no encoder or refuses the map; the caller then copies with cp.async.
-bool ymap_for(hs_ctx* c, int b, CUtensorMap* out) {
+// box (2 ct, 3, min(n2, 256), 1, 1) for the y passes (zax = 0) or (2 ct, 3, 1, min(n3, 256), 1)
+// for the z pass (zax = 1).  Made once per buffer, base and batch shape.  False when the driver
+// offers no encoder or refuses the map; the caller then copies with cp.async.
+bool tile_map(hs_ctx* c, int zax, int b, CUtensorMap* out) {
   const void* base = c->B[b];
   const int n = std::max(1, c->batch_n);
-  if (c->ymap_base[b] != base || c->ymap_stride[b] != c->batch_stride || c->ymap_n[b] != n) {
-    c->ymap_base[b] = base;
-    c->ymap_stride[b] = c->batch_stride;
-    c->ymap_n[b] = n;
-    c->ymap_ok[b] = false;
+  if (c->tmap_base[zax][b] != base || c->tmap_stride[zax][b] != c->batch_stride || c->tmap_n[zax][b] != n) {
+    c->tmap_base[zax][b] = base;
+    c->tmap_stride[zax][b] = c->batch_stride;
+    c->tmap_n[zax][b] = n;
+    c->tmap_ok[zax][b] = false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     const size_t cs = c->f64 ? 16 : 8;
     const size_t row = (size_t)c->P * cs, plane = row * c->n2, comp = plane * c->n3;
+    const int L = zax ? c->n3 : c->n2;
     const cuuint64_t dims[5] = {(cuuint64_t)2 * c->P, 3, (cuuint64_t)c->n2, (cuuint64_t)c->n3, (cuuint64_t)n};
     const cuuint64_t strides[4] = {comp, row, plane, c->batch_stride != 0 ? c->batch_stride : 3 * comp};
-    const cuuint32_t box[5] = {(cuuint32_t)(2 * c->ct), 3, (cuuint32_t)std::min(c->n2, 256), 1, 1};
+    const cuuint32_t box[5] = {(cuuint32_t)(2 * c->ct), 3, zax ? 1u : (cuuint32_t)std::min(L, 256),
+                               zax ? (cuuint32_t)std::min(L, 256) : 1u, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const bool aligned = ((uintptr_t)base % 16 == 0) && (2 * c->ct * (cs / 2)) % 16 == 0 && row % 16 == 0 &&
-                         (c->batch_stride % 16 == 0) && (c->n2 <= 256 || c->n2 % 256 == 0);
+                         (c->batch_stride % 16 == 0) && (L <= 256 || L % 256 == 0);
     if (enc != nullptr && aligned &&
-        enc(&c->ymap[b], c->f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5,
+        enc(&c->tmap[zax][b], c->f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5,
             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-      c->ymap_ok[b] = true;
+      c->tmap_ok[zax][b] = true;
   }
-  if (c->ymap_ok[b]) *out = c->ymap[b];
-  return c->ymap_ok[b];
+  if (c->tmap_ok[zax][b]) *out = c->tmap[zax][b];
+  return c->tmap_ok[zax][b];
 }
 
-// ColArgs of a persistent y pass over B[b]: tensor copies where the option and the map allow
-template <typename T> hs_status set_ymap(hs_ctx* c, hs::ColArgs<T>& a, int b) {
+// ColArgs of a column pass over B[b] (zax: 0 = y passes, only where they run persistent; 1 = z
+// pass, one tile per block with the state read point by point): tensor copies where the option
+// and the map allow
+template <typename T> hs_status set_tile_map(hs_ctx* c, hs::ColArgs<T>& a, int zax, int b) {
   a.tma = 0;
-  if (!c->pipe_y || c->opt.col_copy == 1) return HS_OK;
-  if (ymap_for(c, b, &a.tmap)) {
+  const bool applies = zax == 0 ? c->pipe_y : (!c->pipe_z && !c->zstate_smem);
+  if (!applies || c->opt.col_copy == 1) return HS_OK;
+  if (tile_map(c, zax, b, &a.tmap)) {
     a.tma = 1;
     return HS_OK;
   }
-  if (c->opt.col_copy == 2) return fail(c, HS_ERR_UNSUPPORTED_SIZE, "tensor copies unavailable for the y passes");
+  if (c->opt.col_copy == 2) return fail(c, HS_ERR_UNSUPPORTED_SIZE, "tensor copies unavailable for the column passes");
   return HS_OK;
 }
 
@@ -762,7 +768,7 @@ template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   hs::ColArgs<T> a;
   cudaError_t e;
   fill_col<T>(c, a, c->B[buf], 1);
-  if (hs_status st = set_ymap<T>(c, a, buf); st != HS_OK) return st;
+  if (hs_status st = set_tile_map<T>(c, a, 0, buf); st != HS_OK) return st;
   {
     LaunchScope ls(c, HS_K_YFWD);
     e = c->pipe_y ? hs::launch_colp<T>(a, hs::COL_Y_FWD, c->ct, zg(c, dim3(c->nblk_py)), c->nthr_y, c->smem_py, c->stream)
@@ -770,6 +776,7 @@ template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(y fwd)");
   fill_col<T>(c, a, c->B[buf], 2);
+  if (hs_status st = set_tile_map<T>(c, a, 1, buf); st != HS_OK) return st;
   {
     LaunchScope ls(c, HS_K_ZGREEN);
     e = c->pipe_z ? hs::launch_colp<T>(a, hs::COL_Z_GREEN, c->ct, zg(c, dim3(c->nblk_pz)), c->nthr_z, c->smem_pz,
@@ -778,7 +785,7 @@ template <typename T> hs_status launch_cols(hs_ctx* c, int buf) {
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "k_col(z green)");
   fill_col<T>(c, a, c->B[buf], 1);
-  if (hs_status st = set_ymap<T>(c, a, buf); st != HS_OK) return st;
+  if (hs_status st = set_tile_map<T>(c, a, 0, buf); st != HS_OK) return st;
   {
     LaunchScope ls(c, HS_K_YINV);
     e = c->pipe_y ? hs::launch_colp<T>(a, hs::COL_Y_INV, c->ct, zg(c, dim3(c->nblk_py)), c->nthr_y, c->smem_py, c->stream)
@@ -1397,7 +1404,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
   c->nthr_z = col_threads(c->n3);
   const size_t cs = c->f64 ? 16 : 8;
   c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
-  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs;
+  // the z pass may load its tile by a tensor copy: room for its alignment and barrier
+  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs + hs::kColpTmaSlack;
   c->xfuse = (o.xfuse == 1);
   {
     // radix-5/7/11 lengths run the split path with the default column tile only

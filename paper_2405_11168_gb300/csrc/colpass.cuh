@@ -49,10 +49,11 @@ template <typename T> struct ColArgs {
   size_t zstride;    // batched launches: bytes between the workspaces of consecutive items
   int state_smem;    // COL_Z_GREEN: 1 = the state tile is copied to shared memory beside the force
                      // tile (its copy overlaps the forward transform); 0 = read point by point
-  int tma;           // persistent y passes: tiles loaded by tensor copies described by tmap
+  int tma;           // persistent y passes and the fixed-length z pass: tiles loaded by tensor
+                     // copies described by tmap
   // rank-5 tiled map of buf as T elements: (2P x-values, 3 components, n2, n3, items), box
-  // (2 CT, 3, min(n2, 256), 1, 1); the component dimension sits inside y so that a box lands
-  // as the [e][comp][col] tile
+  // (2 CT, 3, min(n2, 256), 1, 1) for the y passes or (2 CT, 3, 1, min(n3, 256), 1) for the z
+  // pass; the component dimension sits inside y so that a box lands as the [e][comp][col] tile
   CUtensorMap tmap;
 };
 
@@ -263,13 +264,19 @@ __device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cp
 // LF > 0: the transformed length is LF and the block has NT threads, both
 // fixed at compile time (hot sizes); LF = 0: both taken at run time; LF = -1:
 // run time, plans with a radix-5, 7 or 11 stage.
-template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArgs<T> a_) {
+// TMA (z pass with the state read point by point, fixed lengths): thread 0 loads the tile by
+// tensor copies (one per 256 planes) on an mbarrier while every thread issues the state's L2
+// prefetch; the wait is bounded (a timeout is recorded in the status).
+template <typename T, int CT, int MODE, int LF = 0, int NT = 0, bool TMA = false>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid_constant__ ColArgs<T> a_) {
   using C = typename cplx_t<T>::type;
+  static_assert(!TMA || (MODE == COL_Z_GREEN && LF > 0), "tensor copies: fixed-length z pass");
   const ColArgs<T> a = col_item_args(a_);
   if (a.st->retired || (a.skip_if_done && a.st->done)) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);  // [L][3][CT]
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // TMA: the tile starts on a 128-byte boundary and its barrier follows it (kColpTmaSlack)
+  unsigned char* const smb = TMA ? smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u) : smraw;
+  C* sm = reinterpret_cast<C*>(smb);  // [L][3][CT]
   const bool yaxis = (MODE == COL_Y_FWD || MODE == COL_Y_INV);
   const int L = LF > 0 ? LF : (yaxis ? a.n2 : a.n3);
   const int tid = threadIdx.x, nthr = NT > 0 ? NT : (int)blockDim.x;
@@ -289,7 +296,32 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   // flight at once); columns past the row pitch are zero
   constexpr int EPC = 16 / (int)sizeof(C);  // complex values per 16-byte chunk
   constexpr int CPR = CT / EPC;             // chunks per (row, component)
-  for (int i = tid; i < L * 3 * CPR; i += nthr) {
+  if constexpr (TMA) {
+    uint64_t* const tbar = reinterpret_cast<uint64_t*>(smb + (size_t)L * W * sizeof(C));
+    // the copy needs a 128-byte aligned destination and a 64-byte aligned map: checked once,
+    // the pass ends with an error status instead of issuing a misaligned copy
+    if ((smem_u32(sm) & 127u) != 0 || (reinterpret_cast<uintptr_t>(&a_.tmap) & 63u) != 0) {
+      if (tid == 0) a.st->done = DONE_FAULT;
+      return;
+    }
+    if (tid == 0) {
+      mbar_init(tbar, 1);
+      mbar_init_fence();
+      mbar_arrive_expect_tx(tbar, (unsigned)(L * W * sizeof(C)));
+#pragma unroll
+      for (int h = 0; h < (L + 255) / 256; ++h)
+        tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, outer, h * 256, (int)blockIdx.z, tbar);
+    }
+    for (int i = tid; i < L * 3; i += nthr) {
+      const int e = i / 3, c = i - 3 * e;
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    if (!mbar_wait(tbar, 0)) {
+      if (tid == 0) a.st->done = DONE_TIMEOUT;
+    }
+  }
+  for (int i = tid; !TMA && i < L * 3 * CPR; i += nthr) {
     const int e = i / (3 * CPR), rem = i - e * (3 * CPR), c = rem / CPR, col = (rem - c * CPR) * EPC;
     C* dst = sm + e * W + c * CT + col;
     if (col < ccols) {
@@ -301,7 +333,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const ColArg
   }
   cp_async_commit();
   C* ss = nullptr;  // state tile in shared memory (COL_Z_GREEN with state_smem)
-  if (MODE == COL_Z_GREEN) {
+  if (TMA) {
+    // the tile arrived on the barrier above
+  } else if (MODE == COL_Z_GREEN) {
     if (a.state_smem) {
       // the state tile follows the force tile; its copy (a second group) overlaps the forward
       // transform, which waits for the first group only

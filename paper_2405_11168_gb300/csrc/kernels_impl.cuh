@@ -168,6 +168,9 @@ static cudaError_t stencil_f32(const MarchArgs<float>& a, bool iso, int ty, int 
 template <typename T, int CT, int MODE, int LF = 0, int NT = 0>
 static cudaError_t col_one(const ColArgs<T>& a, dim3 g, int nthr, size_t smem, cudaStream_t s) {
   auto k = k_col<T, CT, MODE, LF, NT>;
+  if constexpr (MODE == COL_Z_GREEN && LF > 0) {
+    if (a.tma && !a.state_smem) k = k_col<T, CT, MODE, LF, NT, true>;
+  }
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<g, nthr, smem, s>>>(a);

@@ -29,7 +29,7 @@ template <typename T> struct RowArgs {
   const C* tw;        // w_N1^j
   FftPlan plan;
   int n1, P, nrows;
-  const DevStatus* st;
+  DevStatus* st;
   int skip_if_done;
   size_t zstride;     // batched launches: bytes between the workspaces of consecutive items
 };
@@ -62,6 +62,7 @@ struct RowLayout {
   size_t rowbytes;  // bytes of one input row (C2R: P complex; R2C: n1 real)
   size_t outbytes;  // bytes of one output row (C2R: n1 real; R2C: P complex)
   size_t stage;     // bytes of one staging buffer
+  size_t bar;       // two mbarriers of the staging buffers (bulk-copy loads)
   size_t total;
 };
 __host__ __device__ inline RowLayout row_layout(int mode, int n1, int P, int nthr, int tsize) {
@@ -73,15 +74,19 @@ __host__ __device__ inline RowLayout row_layout(int mode, int n1, int P, int nth
   L.outbytes = (mode == ROW_C2R) ? (size_t)n1 * tsize : (size_t)P * 2 * tsize;
   const size_t rb = L.rowbytes > L.outbytes ? L.rowbytes : L.outbytes;
   L.stage = ((2 * (size_t)L.G * rb) + 15) & ~(size_t)15;
-  L.total = L.zbytes + 2 * L.stage;
+  L.bar = L.zbytes + 2 * L.stage;
+  L.total = L.bar + 16;
   return L;
 }
 
 // Asynchronous copy of batch b (input rows 2bG .. 2bG + 2G - 1, clipped to
 // nrows) into staging buffer `buf`: the rows are one contiguous byte range.
+// bulk: one cp.async.bulk by the calling thread, completing on the buffer's
+// mbarrier (rows of a multiple of 16 bytes); otherwise 16-byte cp.async by
+// every thread and a commit.
 template <typename T, int MODE>
 __device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& L, unsigned char* smraw, int b,
-                                          int buf) {
+                                          int buf, bool bulk = false) {
   const size_t r0 = 2 * (size_t)b * L.G;
   const size_t nr = min((size_t)2 * L.G, (size_t)a.nrows - r0);
   const unsigned char* src = (MODE == ROW_C2R) ? reinterpret_cast<const unsigned char*>(a.spec_in)
@@ -89,6 +94,15 @@ __device__ __forceinline__ void row_stage(const RowArgs<T>& a, const RowLayout& 
   src += r0 * L.rowbytes;
   unsigned char* dst = smraw + L.zbytes + (size_t)buf * L.stage;
   const size_t bytes = nr * L.rowbytes;
+  if (bulk) {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + L.bar) + buf;
+    mbar_arrive_expect_tx(bar, (unsigned)bytes);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"((unsigned)bytes), "r"(smem_u32(bar))
+                 : "memory");
+    return;
+  }
   if ((L.rowbytes & 15) == 0) {
     const int nch = (int)(bytes >> 4);
     for (int i = threadIdx.x; i < nch; i += blockDim.x) cp_async16(dst + 16 * i, src + 16 * i);
@@ -144,13 +158,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
   // buffer and written by one bulk copy (FP64 accumulation keeps per-element
   // updates).  R2C measured faster with direct stores (0.104 vs 0.112 ms at 256^3).
   const bool bulk = LF > 0 && MODE == ROW_C2R && a.acc64 == nullptr && (L.outbytes & 15) == 0;
+  // fixed lengths: each batch arrives by one bulk copy on its staging buffer's mbarrier (waits
+  // bounded; a timeout is recorded in the status)
+  const bool bload = LF > 0 && (L.rowbytes & 15) == 0;
+  uint64_t* sbar = reinterpret_cast<uint64_t*>(smraw + L.bar);
+  bool timed_out = false;
+  if (bload) {
+    if (tid == 0) {
+      mbar_init(sbar, 1);
+      mbar_init(sbar + 1, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
   int buf = 0;
-  if ((int)blockIdx.x < nbatch) row_stage<T, MODE>(a, L, smraw, blockIdx.x, 0);
-  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
-    cp_async_wait_all();
+  if ((int)blockIdx.x < nbatch && (!bload || tid == 0)) row_stage<T, MODE>(a, L, smraw, blockIdx.x, 0, bload);
+  int k = 0;
+  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1, ++k) {
+    if (bload) timed_out |= !mbar_wait(sbar + buf, (unsigned)((k >> 1) & 1));
+    else cp_async_wait_all();
     if (bulk && tid == 0) bulk_wait_read_all();  // staging buffer buf ^ 1 is free again
     __syncthreads();
-    if (b + (int)gridDim.x < nbatch) row_stage<T, MODE>(a, L, smraw, b + gridDim.x, buf ^ 1);
+    if (b + (int)gridDim.x < nbatch && (!bload || tid == 0))
+      row_stage<T, MODE>(a, L, smraw, b + gridDim.x, buf ^ 1, bload);
     unsigned char* stg = smraw + L.zbytes + (size_t)buf * L.stage;
     const size_t nr = min((size_t)2 * G, (size_t)a.nrows - 2 * (size_t)b * G);
     const int s = b * G + grp;
@@ -314,6 +344,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
   }
   cp_async_wait_all();
   if (bulk && tid == 0) bulk_wait_all();
+  if (timed_out) a.st->done = DONE_TIMEOUT;
 }
 
 }  // namespace hs

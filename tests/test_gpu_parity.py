@@ -250,12 +250,13 @@ def test_deterministic_repeat(hs):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
-@pytest.mark.parametrize("grid", [(40, 128, 12), (24, 256, 6), (20, 512, 6)])
-def test_y_pass_tensor_copies_match_cp_async(hs, prec, grid):
-    """The persistent y passes' tiles loaded by tensor (TMA) copies give bit-identical
-    iterates, fields and errors to the 16-byte cp.async loads, in FP64, FP32 and refined mode,
-    on y lengths 128, 256 and 512 (two copies per tile) with ragged x tiles (the last tile of 8
-    or 4 columns partly past the row pitch, filled with zeros by the copy)."""
+@pytest.mark.parametrize("grid", [(40, 128, 64), (24, 64, 256), (20, 512, 128)])
+def test_column_tensor_copies_match_cp_async(hs, prec, grid):
+    """Column-pass tiles loaded by tensor (TMA) copies (persistent y passes of length 128 and
+    512, the latter in two copies per tile; z passes of length 64, 256 and 128) give
+    bit-identical iterates, fields and errors to the 16-byte cp.async loads, in FP64, FP32 and
+    refined mode, with ragged x tiles (the last tile of 8 or 4 columns partly past the row
+    pitch, filled with zeros by the copy)."""
     ids = synth.random_phase_map(tuple(grid), 2, seed=7)
     table = synth.two_phase_table(1.0, 0.3, 6.0, 0.3)
     runs = []
