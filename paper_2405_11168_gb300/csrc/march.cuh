@@ -181,7 +181,7 @@ __device__ __forceinline__ void tetra_strain_fast(const T (&u)[2][2][2][3], cons
 
 // Shared-memory layout of k_march (host and device use the same function).
 struct MarchLayout {
-  size_t ring, fbuf, stage, ids, src, edge, red, total;
+  size_t ring, fbuf, stage, ids, src, edge, red, bar, total;
   int n1i, n1s;  // row pitches (elements) of the ids and source stages
 };
 
@@ -209,6 +209,8 @@ __host__ __device__ inline MarchLayout march_layout(int n1, int P, int nthr, int
   off += hs_align16((size_t)tsize * (nthr / 32) * (ty + 1) * 12);
   L.red = off;
   off += 32 * NRED * 8;
+  L.bar = off;  // three mbarriers (bulk plane copies of the FP32 real-space pass)
+  off += 32;
   L.total = off;
   return L;
 }

@@ -132,6 +132,57 @@ __device__ __forceinline__ void stencil_prefetch(const MarchArgs<float>& a, cons
   cp_async_commit();
 }
 
+// One bulk copy of rows y, y + 1, ... of a plane (the rows of y0 + r0 .. y0 + r1 - 1, each
+// wrapped into [0, n2)) into consecutive shared rows: split where the wrap breaks contiguity.
+// Issued by one thread; completes on bar.
+__device__ __forceinline__ void bulk_rows(unsigned char* dst, const unsigned char* plane, int y_first, int nrows,
+                                          int n2, unsigned rowbytes, uint64_t* bar) {
+  int y = y_first, r = 0;
+  y += (y < 0) ? n2 : 0;
+  y -= (y >= n2) ? n2 : 0;
+  while (r < nrows) {
+    const int run = min(nrows - r, n2 - y);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst + (size_t)r * rowbytes)),
+                 "l"(plane + (size_t)y * rowbytes), "r"((unsigned)run * rowbytes), "r"(smem_u32(bar))
+                 : "memory");
+    r += run;
+    y = 0;
+  }
+}
+
+// The plane copies of stencil_prefetch as bulk copies by the calling thread (compile-time N1,
+// a multiple of 8): per component one run of rows (two or three where y wraps), the id rows
+// and the source rows likewise, all completing on the ring slot's mbarrier.
+template <int TY, int N1>
+__device__ __forceinline__ void stencil_prefetch_bulk(const MarchArgs<float>& a, const MarchLayout& lay,
+                                                      unsigned char* smraw, int y0, int pu, int slot, int ib, int ps,
+                                                      bool want_ids, uint64_t* bar) {
+  constexpr int NR = TY + 2;
+  const int n2 = a.n2, n3 = a.n3;
+  const size_t rplane = (size_t)n2 * N1, rcomp = (size_t)n3 * rplane;
+  const int gz = pu < 0 ? pu + n3 : (pu >= n3 ? pu - n3 : pu);
+  const bool src = a.src != nullptr && ps >= 0;
+  mbar_arrive_expect_tx(bar, (unsigned)(3 * NR * N1 * 4 + (want_ids ? (TY + 1) * N1 * 2 : 0) +
+                                        (src ? 3 * TY * N1 * 4 : 0)));
+  unsigned char* ring = smraw + lay.ring + (size_t)slot * 3 * NR * N1 * 4;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    bulk_rows(ring + (size_t)c * NR * N1 * 4,
+              reinterpret_cast<const unsigned char*>(a.ureal + c * rcomp + (size_t)gz * rplane), y0 - 1, NR, n2,
+              N1 * 4, bar);
+  if (want_ids)
+    bulk_rows(smraw + lay.ids + (size_t)ib * (TY + 1) * N1 * 2,
+              reinterpret_cast<const unsigned char*>(a.ids + (size_t)gz * rplane), y0, TY + 1, n2, N1 * 2, bar);
+  if (src) {
+    const size_t zs = (size_t)(ps % n3) * rplane;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      bulk_rows(smraw + lay.src + ((size_t)ib * 3 * TY + (size_t)c * TY) * N1 * 4,
+                reinterpret_cast<const unsigned char*>(a.src + c * rcomp + zs), y0, TY, n2, N1 * 4, bar);
+  }
+}
+
 // N1 > 0: the x extent is a compile-time constant (hot sizes), so shared
 // memory row offsets become immediates; N1 = 0: taken at run time.
 // BATCH: a batched launch (grid.z items, every workspace pointer moved per item);
@@ -186,16 +237,47 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a_, cons
   const bool recv_edge = xact && !recv_shfl;
   const int src_warp = ((x + 1) % n1) >> 5;
 
-  stencil_prefetch<TY, N1>(a, lay, smraw, y0, z0 - 1, 0, 0, -1, false);
-  stencil_prefetch<TY, N1>(a, lay, smraw, y0, z0, 1, 0, -1, true);
+  // compile-time x extents (a multiple of 8): planes arrive by bulk copies from thread 0, plane
+  // q in ring slot (q - z0 + 1) % 3 completing on that slot's mbarrier (waits bounded; a
+  // timeout is recorded in the status)
+  constexpr bool BULK = N1 > 0 && N1 % 8 == 0;
+  uint64_t* const pbar = reinterpret_cast<uint64_t*>(smraw + lay.bar);
+  bool timed_out = false;
+  if (BULK) {
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) mbar_init(pbar + q, 1);
+      mbar_init_fence();
+      stencil_prefetch_bulk<TY, (BULK ? N1 : 8)>(a, lay, smraw, y0, z0 - 1, 0, 0, -1, false, pbar);
+      stencil_prefetch_bulk<TY, (BULK ? N1 : 8)>(a, lay, smraw, y0, z0, 1, 0, -1, true, pbar + 1);
+    }
+    __syncthreads();  // the barriers are initialised before anyone waits on them
+  } else {
+    stencil_prefetch<TY, N1>(a, lay, smraw, y0, z0 - 1, 0, 0, -1, false);
+    stencil_prefetch<TY, N1>(a, lay, smraw, y0, z0, 1, 0, -1, true);
+  }
 
   const int pend = (MODE == MODE_FORCE) ? z0 + zc : z0 + zc - 1;
   for (int p = z0; p <= pend; ++p) {
     const int ib = (p - z0) & 1;
-    cp_async_wait_all();
-    __syncthreads();
     const int sc = (p - z0 + 1) % 3, sp = (p - z0) % 3;
-    if (p < pend) stencil_prefetch<TY, N1>(a, lay, smraw, y0, p + 1, (p - z0 + 2) % 3, ib ^ 1, MODE == MODE_FORCE ? p : -1, true);
+    if (BULK) {
+      if (p == z0) timed_out |= !mbar_wait(pbar, 0);
+      timed_out |= !mbar_wait(pbar + sc, (unsigned)(((p - z0 + 1) / 3) & 1));
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    if (p < pend) {
+      if (BULK) {
+        if (tid == 0)
+          stencil_prefetch_bulk<TY, (BULK ? N1 : 8)>(a, lay, smraw, y0, p + 1, (p - z0 + 2) % 3, ib ^ 1,
+                                                     MODE == MODE_FORCE ? p : -1, true, pbar + (p - z0 + 2) % 3);
+      } else {
+        stencil_prefetch<TY, N1>(a, lay, smraw, y0, p + 1, (p - z0 + 2) % 3, ib ^ 1, MODE == MODE_FORCE ? p : -1,
+                                 true);
+      }
+    }
     const int pz = p % n3;
     const bool own_plane = p < z0 + zc;
     const uint16_t* idrow = sids + (size_t)ib * (TY + 1) * n1i;
@@ -380,6 +462,7 @@ __global__ void __launch_bounds__(512) k_stencil(const MarchArgs<float> a_, cons
       for (int k = 0; k < 3; ++k) { Fp[r][k] = Fn[r][k]; Fn[r][k] = 0.f; }
   }
   cp_async_wait_all();
+  if (BULK && timed_out) a.st->done = DONE_TIMEOUT;
   if (MODE != MODE_FORCE) return;
   double acc[NRED];
 #pragma unroll
