@@ -107,7 +107,8 @@ typedef struct {
                            transform (twice the tile's shared memory); results do not change */
   int col_pipe;         /* y passes at lengths 128, 256, 512 with the default tile: 0 = persistent
                            blocks that copy the next tile while transforming the current one
-                           (default), 1 = one tile per block; results do not change */
+                           (default), 1 = one tile per block, 2 = persistent y passes and a
+                           persistent z pass (z lengths 128, 256, 512); results do not change */
   int col_copy;         /* tile loads of the persistent y passes (y lengths 128, 256, 512) and of the
                            z pass (z lengths 64, 128, 256, 512, state read point by point): 0 = tensor
                            (TMA) copies where the driver encodes the tile map, else 16-byte cp.async

@@ -754,7 +754,7 @@ bool tile_map(hs_ctx* c, int zax, int b, CUtensorMap* out) {
 // and the map allow
 template <typename T> hs_status set_tile_map(hs_ctx* c, hs::ColArgs<T>& a, int zax, int b) {
   a.tma = 0;
-  const bool applies = zax == 0 ? c->pipe_y : (!c->pipe_z && !c->zstate_smem);
+  const bool applies = zax == 0 ? c->pipe_y : !c->zstate_smem;
   if (!applies || c->opt.col_copy == 1) return HS_OK;
   if (tile_map(c, zax, b, &a.tmap)) {
     a.tma = 1;
@@ -1244,7 +1244,7 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       !(o.ytile == 0 || ((o.ytile == 2 || o.ytile == 4 || o.ytile == 8) && grid[1] % o.ytile == 0)) ||
       (o.xfuse != 0 && o.xfuse != 1) || o.col_tile < 0 || o.col_threads < 0 || (o.col_threads % 32) != 0 ||
       (o.use_graphs != 0 && o.use_graphs != 1) || o.col_state < 0 || o.col_state > 2 ||
-      (o.col_pipe != 0 && o.col_pipe != 1) || o.col_copy < 0 || o.col_copy > 2)
+      o.col_pipe < 0 || o.col_pipe > 2 || o.col_copy < 0 || o.col_copy > 2)
     return fail(nullptr, HS_ERR_INVALID_ARG, "bad options");
   if (m->kind != HS_IDS_U8 && m->kind != HS_IDS_U16) return fail(nullptr, HS_ERR_INVALID_ARG, "bad id kind");
   if (m->nphase < 1 || m->nphase > HS_MAX_PHASES)
@@ -1527,11 +1527,12 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
     // the z pass stays one tile per block: its Green step waits on the state point by point, and
     // three resident blocks hide that better than two persistent ones (256^3 FP32: 0.228 against
     // 0.247 ms; the y passes gain, 0.095 against 0.101 ms)
-    for (int axis = 1; axis <= 1 && o.col_pipe == 0 && !ext && nsm > 0; ++axis) {
-      const int L = c->n2;
+    for (int axis = 1; axis <= (o.col_pipe == 2 ? 2 : 1) && o.col_pipe != 1 && !ext && nsm > 0; ++axis) {
+      const int L = axis == 1 ? c->n2 : c->n3;
       if (L != 128 && L != 256 && L != 512) continue;
-      // the y passes may load their tiles by tensor copies: room for their alignment and barriers
-      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + (axis == 1 ? hs::kColpTmaSlack : 0);
+      if (axis == 2 && c->zstate_smem) continue;  // the persistent z pass reads the state point by point
+      // the tiles may arrive by tensor copies: room for their alignment and barriers
+      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + hs::kColpTmaSlack;
       if (smem > (size_t)smem_optin) continue;
       const int nthr = axis == 1 ? c->nthr_y : c->nthr_z;
       int per_sm = 0;

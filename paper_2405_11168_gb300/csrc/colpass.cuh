@@ -419,7 +419,7 @@ template <typename T, int CT, int MODE, int LF, int NT, bool TMA = false>
 __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<T> a_) {
   using C = typename cplx_t<T>::type;
   static_assert(LF > 0 && MODE != COL_Z_INV_STATE, "persistent column pass: fixed lengths, iteration modes");
-  static_assert(!TMA || MODE == COL_Y_FWD || MODE == COL_Y_INV, "tensor copies: y passes");
+  static_assert(!TMA || MODE == COL_Y_FWD || MODE == COL_Y_INV || MODE == COL_Z_GREEN, "tensor copies");
   const ColArgs<T> a = col_item_args(a_);
   if (a.st->retired || (a.skip_if_done && a.st->done)) return;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -447,6 +447,15 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
   const int xtiles = (a.nh + CT - 1) / CT;
   const int ntiles = xtiles * (yaxis ? a.n3 : a.n2);
   const C* __restrict__ tw = a.tw;
+  // the Green step reads the state tile of tile t after its forward transform: into L2 early
+  auto prefetch_state = [&](int t) {
+    const int x0 = (t % xtiles) * CT, outer = t / xtiles;
+    const size_t base = yaxis ? (size_t)outer * plane + x0 : (size_t)outer * a.P + x0;
+    for (int i = tid; i < L * 3; i += NT) {
+      const int e = i / 3, c = i - 3 * e;
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
+    }
+  };
   auto load = [&](int t, C* sm) {
     const int x0 = (t % xtiles) * CT, outer = t / xtiles;
     const size_t base = yaxis ? (size_t)outer * plane + x0 : (size_t)outer * a.P + x0;
@@ -461,12 +470,7 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
         for (int q = 0; q < EPC; ++q) dst[q] = cmk<C>(0, 0);
       }
     }
-    if (MODE == COL_Z_GREEN) {
-      for (int i = tid; i < L * 3; i += NT) {
-        const int e = i / 3, c = i - 3 * e;
-        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
-      }
-    }
+    if (MODE == COL_Z_GREEN) prefetch_state(t);
   };
   // tile t into buffer b by tensor copies (thread 0)
   auto load_tma = [&](int t, int b) {
@@ -474,8 +478,10 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     C* sm = sm0 + (size_t)b * L * W;
     mbar_arrive_expect_tx(&tbar[b], (unsigned)(L * W * sizeof(C)));
 #pragma unroll
-    for (int h = 0; h < (L + 255) / 256; ++h)
-      tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, h * 256, outer, (int)blockIdx.z, &tbar[b]);
+    for (int h = 0; h < (L + 255) / 256; ++h) {
+      if (yaxis) tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, h * 256, outer, (int)blockIdx.z, &tbar[b]);
+      else tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, outer, h * 256, (int)blockIdx.z, &tbar[b]);
+    }
   };
   bool timed_out = false;
   int t = blockIdx.x;
@@ -487,6 +493,7 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     }
     __syncthreads();
     if (tid == 0 && t < ntiles) load_tma(t, 0);
+    if (MODE == COL_Z_GREEN && t < ntiles) prefetch_state(t);
   } else {
     if (t < ntiles) load(t, sm0);
     cp_async_commit();
@@ -496,6 +503,7 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     // the other buffer was freed by the barrier that ended the previous tile
     if constexpr (TMA) {
       if (tid == 0 && t + (int)gridDim.x < ntiles) load_tma(t + gridDim.x, (k + 1) & 1);
+      if (MODE == COL_Z_GREEN && t + (int)gridDim.x < ntiles) prefetch_state(t + gridDim.x);
       timed_out |= !mbar_wait(&tbar[k & 1], (unsigned)((k >> 1) & 1));
     } else {
       if (t + (int)gridDim.x < ntiles) load(t + gridDim.x, sm0 + (size_t)((k + 1) & 1) * L * W);
@@ -514,7 +522,11 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     io.ncol = min(CT, a.nh - x0);
     if (MODE == COL_Z_GREEN) {
       fft_col_fixed<LF, W, CT, false, false, false>(sm, io, tw, tid, NT);
-      col_green<T, CT>(a, sm, nullptr, base, rstride, cstride, x0, outer, io.ncol, L, tid, NT);
+      if constexpr (NT % CT == 0 && (LF * CT) % NT == 0) {
+        col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, io.ncol, tid);
+      } else {
+        col_green<T, CT>(a, sm, nullptr, base, rstride, cstride, x0, outer, io.ncol, L, tid, NT);
+      }
       __syncthreads();
       fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, NT);
     } else {

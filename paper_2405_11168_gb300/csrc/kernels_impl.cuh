@@ -217,9 +217,7 @@ static cudaError_t col_dispatch(const ColArgs<T>& a, int mode, dim3 g, int nthr,
 template <typename T, int CT, int MODE, int LF, int NT>
 static cudaError_t colp_one(const ColArgs<T>& a, dim3 g, size_t smem, cudaStream_t s, int* occ) {
   auto k = k_colp<T, CT, MODE, LF, NT>;
-  if constexpr (MODE == COL_Y_FWD || MODE == COL_Y_INV) {
-    if (a.tma) k = k_colp<T, CT, MODE, LF, NT, true>;
-  }
+  if (a.tma) k = k_colp<T, CT, MODE, LF, NT, true>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   if (occ != nullptr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, smem);

@@ -176,7 +176,7 @@ def test_create_rejects_null_coefficient_field(lib):
 @pytest.mark.parametrize("field,value", [
     ("check_every", 0), ("inner_max", 0), ("inner_ratio", 0.0), ("inner_ratio", 1.0), ("zchunk", -1),
     ("ytile", 3), ("ytile", 16), ("xfuse", 2), ("col_tile", -1), ("col_tile", 12), ("col_threads", 48),
-    ("col_threads", 4096), ("use_graphs", 2), ("col_copy", -1), ("col_copy", 3),
+    ("col_threads", 4096), ("use_graphs", 2), ("col_copy", -1), ("col_copy", 3), ("col_pipe", 3),
 ])
 def test_create_rejects_bad_options_before_any_device_work(lib, field, value):
     from paper_2405_11168_gb300 import hs

@@ -253,23 +253,25 @@ def test_deterministic_repeat(hs):
 @pytest.mark.parametrize("grid", [(40, 128, 64), (24, 64, 256), (20, 512, 128)])
 def test_column_tensor_copies_match_cp_async(hs, prec, grid):
     """Column-pass tiles loaded by tensor (TMA) copies (persistent y passes of length 128 and
-    512, the latter in two copies per tile; z passes of length 64, 256 and 128) give
-    bit-identical iterates, fields and errors to the 16-byte cp.async loads, in FP64, FP32 and
-    refined mode, with ragged x tiles (the last tile of 8 or 4 columns partly past the row
-    pitch, filled with zeros by the copy)."""
+    512, the latter in two copies per tile; z passes of length 64, 256 and 128, one tile per
+    block or persistent) give bit-identical iterates, fields and errors to the 16-byte cp.async
+    loads, in FP64, FP32 and refined mode, with ragged x tiles (the last tile of 8 or 4 columns
+    partly past the row pitch, filled with zeros by the copy)."""
     ids = synth.random_phase_map(tuple(grid), 2, seed=7)
     table = synth.two_phase_table(1.0, 0.3, 6.0, 0.3)
     runs = []
-    for copy in (1, 2):
-        s = hs.Solver(ids, table, precision=prec, col_copy=copy, inner_max=8)
+    # cp.async loads; tensor copies; tensor copies with a persistent z pass (z lengths 128, 256)
+    for copy, pipe in ((1, 0), (2, 0), (2, 2)):
+        s = hs.Solver(ids, table, precision=prec, col_copy=copy, col_pipe=pipe, inner_max=8)
         out = s.solve(E_MIX, tol=1e-9, max_iter=30)
         runs.append((out["iters"], out["err"], out["sig_eff"].copy(), out["eps"].cpu().numpy(),
                      out["sig"].cpu().numpy(), s.err_history().copy()))
         s.close()
-    a, b = runs
-    assert a[0] == b[0] and a[1] == b[1]
-    for i in (2, 3, 4, 5):
-        np.testing.assert_array_equal(a[i], b[i])
+    a = runs[0]
+    for b in runs[1:]:
+        assert a[0] == b[0] and a[1] == b[1]
+        for i in (2, 3, 4, 5):
+            np.testing.assert_array_equal(a[i], b[i])
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
