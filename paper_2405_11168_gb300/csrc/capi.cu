@@ -1405,7 +1405,7 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
   const size_t cs = c->f64 ? 16 : 8;
   c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
   // the z pass may load its tile by a tensor copy: room for its alignment and barrier
-  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs + hs::kColpTmaSlack;
+  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs + hs::kColpTmaSlack + (size_t)c->n3 * cs;
   c->xfuse = (o.xfuse == 1);
   {
     // radix-5/7/11 lengths run the split path with the default column tile only

@@ -316,6 +316,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
       const int e = i / 3, c = i - 3 * e;
       asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
     }
+    // the transforms' twiddle table, copied behind the tile's barrier
+    C* const tws = reinterpret_cast<C*>(smb + (size_t)L * W * sizeof(C) + 16);
+    for (int i = tid; i < L; i += nthr) tws[i] = __ldg(tw + i);
     __syncthreads();  // the barrier is initialised before anyone waits on it
     if (!mbar_wait(tbar, 0)) {
       if (tid == 0) a.st->done = DONE_TIMEOUT;
@@ -368,8 +371,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
     io.rstride = rstride;
     io.ccols = ccols;
     io.ncol = ncol;
+    const C* const twf = TMA ? reinterpret_cast<const C*>(smb + (size_t)L * W * sizeof(C) + 16) : tw;
     if (MODE == COL_Z_GREEN) {
-      fft_col_fixed<LF, W, CT, false, false, false>(sm, io, tw, tid, nthr);
+      fft_col_fixed<LF, W, CT, false, false, false, TMA>(sm, io, twf, tid, nthr);
       if (ss != nullptr) {
         cp_async_wait_all();
         __syncthreads();
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
         col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
       }
       __syncthreads();
-      fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, nthr);
+      fft_col_fixed<LF, W, CT, true, false, true, TMA>(sm, io, twf, tid, nthr);
     } else {
       fft_col_fixed<LF, W, CT, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, false, true>(sm, io, tw, tid, nthr);
     }

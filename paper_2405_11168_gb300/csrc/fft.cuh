@@ -438,7 +438,21 @@ template <typename C> struct ColIO {
   int ccols, ncol;
 };
 
-template <int L, int R, int NS, int W, int CT, bool INV, bool FROM_G, bool TO_G, typename C>
+// twiddle i of the table: from global memory through the read-only path, or (TWS) from a copy
+// of the table in shared memory
+template <bool TWS, typename C> __device__ __forceinline__ C tw_load(const C* __restrict__ tw, int i) {
+  if constexpr (TWS) {
+    C w;
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(tw + i));
+    if constexpr (sizeof(C) == 8) asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(w.x), "=f"(w.y) : "r"(a));
+    else asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(w.x), "=d"(w.y) : "r"(a));
+    return w;
+  } else {
+    return __ldg(tw + i);
+  }
+}
+
+template <int L, int R, int NS, int W, int CT, bool INV, bool FROM_G, bool TO_G, bool TWS = false, typename C>
 __device__ __forceinline__ void stage_col(C* sm, const ColIO<C>& io, int s, int t, bool active,
                                           const C* __restrict__ tw) {
   constexpr int T = L / kE;
@@ -475,7 +489,7 @@ __device__ __forceinline__ void stage_col(C* sm, const ColIO<C>& io, int s, int 
       if (NS > 1) {
 #pragma unroll
         for (int m = 1; m < R; ++m) {
-          C w = __ldg(tw + kk * m * step);
+          C w = tw_load<TWS>(tw, kk * m * step);
           if (INV) w.y = -w.y;
           v[k][m] = cmul(v[k][m], w);
         }
@@ -497,19 +511,20 @@ __device__ __forceinline__ void stage_col(C* sm, const ColIO<C>& io, int s, int 
   if (!TO_G) __syncthreads();
 }
 
-template <int L, int ST, int NS, int W, int CT, bool INV, bool IN_G, bool OUT_G, typename C>
+template <int L, int ST, int NS, int W, int CT, bool INV, bool IN_G, bool OUT_G, bool TWS = false, typename C>
 __device__ __forceinline__ void stages_col(C* sm, const ColIO<C>& io, int s, int t, bool active,
                                            const C* __restrict__ tw) {
   if constexpr (ST < FixedPlan<L>::n) {
     constexpr int R = FixedPlan<L>::r(ST);
     constexpr bool FIRST = (ST == 0), LAST = (ST + 1 == FixedPlan<L>::n);
-    stage_col<L, R, NS, W, CT, INV, IN_G && FIRST, OUT_G && LAST>(sm, io, s, t, active, tw);
-    stages_col<L, ST + 1, NS * R, W, CT, INV, IN_G, OUT_G>(sm, io, s, t, active, tw);
+    stage_col<L, R, NS, W, CT, INV, IN_G && FIRST, OUT_G && LAST, TWS>(sm, io, s, t, active, tw);
+    stages_col<L, ST + 1, NS * R, W, CT, INV, IN_G, OUT_G, TWS>(sm, io, s, t, active, tw);
   }
 }
 
 // FFT of the W = 3 * CT columns of a tile; lanes walk across columns (COLMAP).
-template <int L, int W, int CT, bool INV, bool IN_G, bool OUT_G, typename C>
+// TWS: tw points to a copy of the twiddle table in shared memory.
+template <int L, int W, int CT, bool INV, bool IN_G, bool OUT_G, bool TWS = false, typename C>
 __device__ __forceinline__ void fft_col_fixed(C* sm, const ColIO<C>& io, const C* __restrict__ tw, int tid,
                                               int nthreads) {
   constexpr int T = L / kE;
@@ -518,7 +533,7 @@ __device__ __forceinline__ void fft_col_fixed(C* sm, const ColIO<C>& io, const C
     const int sl = tid % G, t = tid / G;
     const int s = g0 + sl;
     const bool active = t < T && s < W;
-    stages_col<L, 0, 1, W, CT, INV, IN_G, OUT_G>(sm, io, s, t, active, tw);
+    stages_col<L, 0, 1, W, CT, INV, IN_G, OUT_G, TWS>(sm, io, s, t, active, tw);
   }
 }
 
