@@ -1532,7 +1532,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       if (L != 128 && L != 256 && L != 512) continue;
       if (axis == 2 && c->zstate_smem) continue;  // the persistent z pass reads the state point by point
       // the tiles may arrive by tensor copies: room for their alignment and barriers
-      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + hs::kColpTmaSlack;
+      // and for the twiddle table behind them
+      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + hs::kColpTmaSlack + (size_t)L * cs;
       if (smem > (size_t)smem_optin) continue;
       const int nthr = axis == 1 ? c->nthr_y : c->nthr_z;
       int per_sm = 0;

@@ -450,7 +450,6 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
   const size_t rstride = yaxis ? (size_t)a.P : plane;
   const int xtiles = (a.nh + CT - 1) / CT;
   const int ntiles = xtiles * (yaxis ? a.n3 : a.n2);
-  const C* __restrict__ tw = a.tw;
   // the Green step reads the state tile of tile t after its forward transform: into L2 early
   auto prefetch_state = [&](int t) {
     const int x0 = (t % xtiles) * CT, outer = t / xtiles;
@@ -487,6 +486,9 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
       else tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, outer, h * 256, (int)blockIdx.z, &tbar[b]);
     }
   };
+  // the transforms' twiddle table, copied behind the barriers (read after the first barrier)
+  C* const tws = reinterpret_cast<C*>(smb + (size_t)2 * L * W * sizeof(C) + 16);
+  for (int i = tid; i < L; i += NT) tws[i] = __ldg(a.tw + i);
   bool timed_out = false;
   int t = blockIdx.x;
   if constexpr (TMA) {
@@ -525,16 +527,16 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     io.ccols = min(CT, a.P - x0);
     io.ncol = min(CT, a.nh - x0);
     if (MODE == COL_Z_GREEN) {
-      fft_col_fixed<LF, W, CT, false, false, false>(sm, io, tw, tid, NT);
+      fft_col_fixed<LF, W, CT, false, false, false, true>(sm, io, tws, tid, NT);
       if constexpr (NT % CT == 0 && (LF * CT) % NT == 0) {
         col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, io.ncol, tid);
       } else {
         col_green<T, CT>(a, sm, nullptr, base, rstride, cstride, x0, outer, io.ncol, L, tid, NT);
       }
       __syncthreads();
-      fft_col_fixed<LF, W, CT, true, false, true>(sm, io, tw, tid, NT);
+      fft_col_fixed<LF, W, CT, true, false, true, true>(sm, io, tws, tid, NT);
     } else {
-      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV, false, true>(sm, io, tw, tid, NT);
+      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV, false, true, true>(sm, io, tws, tid, NT);
     }
     // this tile's shared writes come before the tensor copy that refills the buffer
     if (TMA) fence_async_smem();

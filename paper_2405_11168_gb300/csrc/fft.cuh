@@ -341,8 +341,22 @@ template <int NS, int R> __device__ __forceinline__ int stockham_out(int b) {
   return ((b >> ilog2_c(NS)) << (ilog2_c(NS) + ilog2_c(R))) | (b & (NS - 1));
 }
 
+// twiddle i of the table: from global memory through the read-only path, or (TWS) from a copy
+// of the table in shared memory
+template <bool TWS, typename C> __device__ __forceinline__ C tw_load(const C* __restrict__ tw, int i) {
+  if constexpr (TWS) {
+    C w;
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(tw + i));
+    if constexpr (sizeof(C) == 8) asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(w.x), "=f"(w.y) : "r"(a));
+    else asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(w.x), "=d"(w.y) : "r"(a));
+    return w;
+  } else {
+    return __ldg(tw + i);
+  }
+}
+
 // one stage; sequence s element e at buf[s*SS + seq_pos<ES, PS>(e)]
-template <int L, int R, int NS, int SS, int ES, int PS, bool INV, typename C>
+template <int L, int R, int NS, int SS, int ES, int PS, bool INV, bool TWS = false, typename C>
 __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, const C* __restrict__ tw, bool wsync) {
   constexpr int T = L / kE;
   constexpr int nb = L / R;
@@ -378,7 +392,7 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
       if (NS > 1) {
 #pragma unroll
         for (int m = 1; m < R; ++m) {
-          C w = __ldg(tw + kk * m * step);
+          C w = tw_load<TWS>(tw, kk * m * step);
           if (INV) w.y = -w.y;
           v[k][m] = cmul(v[k][m], w);
         }
@@ -396,18 +410,19 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
   if (wsync) __syncwarp(); else __syncthreads();
 }
 
-template <int L, int ST, int NS, int SS, int ES, int PS, bool INV, typename C>
+template <int L, int ST, int NS, int SS, int ES, int PS, bool INV, bool TWS = false, typename C>
 __device__ __forceinline__ void stages_fixed(C* buf, int s, int t, bool active, const C* __restrict__ tw,
                                              bool wsync) {
   if constexpr (ST < FixedPlan<L>::n) {
     constexpr int R = FixedPlan<L>::r(ST);
-    stage_fixed<L, R, NS, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
-    stages_fixed<L, ST + 1, NS * R, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
+    stage_fixed<L, R, NS, SS, ES, PS, INV, TWS>(buf, s, t, active, tw, wsync);
+    stages_fixed<L, ST + 1, NS * R, SS, ES, PS, INV, TWS>(buf, s, t, active, tw, wsync);
   }
 }
 
-// Same contract as fft_smem with L, the strides and the mapping fixed at compile time.
-template <int L, bool INV, bool COLMAP, int SS, int ES, int PS, typename C>
+// Same contract as fft_smem with L, the strides and the mapping fixed at compile time.  TWS: tw
+// points to a copy of the twiddle table in shared memory.
+template <int L, bool INV, bool COLMAP, int SS, int ES, int PS, bool TWS = false, typename C>
 __device__ __forceinline__ void fft_fixed(C* buf, int nseq, const C* __restrict__ tw, int tid, int nthreads) {
   constexpr int T = L / kE;
   const int G = nthreads / T;
@@ -417,7 +432,7 @@ __device__ __forceinline__ void fft_fixed(C* buf, int nseq, const C* __restrict_
     const int t = COLMAP ? (tid / G) : (tid % T);
     const int s = g0 + sl;
     const bool active = (COLMAP ? (t < T) : (sl < G)) && s < nseq;
-    stages_fixed<L, 0, 1, SS, ES, PS, INV>(buf, s, t, active, tw, wsync);
+    stages_fixed<L, 0, 1, SS, ES, PS, INV, TWS>(buf, s, t, active, tw, wsync);
   }
 }
 
@@ -437,20 +452,6 @@ template <typename C> struct ColIO {
   size_t cstride, rstride;
   int ccols, ncol;
 };
-
-// twiddle i of the table: from global memory through the read-only path, or (TWS) from a copy
-// of the table in shared memory
-template <bool TWS, typename C> __device__ __forceinline__ C tw_load(const C* __restrict__ tw, int i) {
-  if constexpr (TWS) {
-    C w;
-    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(tw + i));
-    if constexpr (sizeof(C) == 8) asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(w.x), "=f"(w.y) : "r"(a));
-    else asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(w.x), "=d"(w.y) : "r"(a));
-    return w;
-  } else {
-    return __ldg(tw + i);
-  }
-}
 
 template <int L, int R, int NS, int W, int CT, bool INV, bool FROM_G, bool TO_G, bool TWS = false, typename C>
 __device__ __forceinline__ void stage_col(C* sm, const ColIO<C>& io, int s, int t, bool active,

@@ -63,6 +63,7 @@ struct RowLayout {
   size_t outbytes;  // bytes of one output row (C2R: n1 real; R2C: P complex)
   size_t stage;     // bytes of one staging buffer
   size_t bar;       // two mbarriers of the staging buffers (bulk-copy loads)
+  size_t tws;       // the twiddle table (n1 complex values; fixed lengths)
   size_t total;
 };
 __host__ __device__ inline RowLayout row_layout(int mode, int n1, int P, int nthr, int tsize) {
@@ -75,7 +76,8 @@ __host__ __device__ inline RowLayout row_layout(int mode, int n1, int P, int nth
   const size_t rb = L.rowbytes > L.outbytes ? L.rowbytes : L.outbytes;
   L.stage = ((2 * (size_t)L.G * rb) + 15) & ~(size_t)15;
   L.bar = L.zbytes + 2 * L.stage;
-  L.total = L.bar + 16;
+  L.tws = L.bar + 16;
+  L.total = L.tws + (size_t)n1 * 2 * tsize;
   return L;
 }
 
@@ -171,6 +173,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
     }
     __syncthreads();
   }
+  // fixed lengths: the transforms read the twiddle table from a copy in shared memory (first read
+  // after the barrier that opens the first batch)
+  C* const tws = reinterpret_cast<C*>(smraw + L.tws);
+  if constexpr (LF > 0) {
+    for (int i = tid; i < n1; i += nthr) tws[i] = __ldg(a.tw + i);
+  }
   int buf = 0;
   if ((int)blockIdx.x < nbatch && (!bload || tid == 0)) row_stage<T, MODE>(a, L, smraw, blockIdx.x, 0, bload);
   int k = 0;
@@ -216,7 +224,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       }
       group_sync(wsync);
       if constexpr (LF > 0) {
-        fft_fixed<LF, true, false, FP, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+        fft_fixed<LF, true, false, FP, 1, -2, true>(reinterpret_cast<C*>(smraw), G, tws, tid, nthr);
       } else {
         fft_smem<true, false, (LF < 0)>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                               tid, nthr);
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
       }
       group_sync(wsync);
       if constexpr (LF > 0) {
-        fft_fixed<LF, false, false, FP, 1, -2>(reinterpret_cast<C*>(smraw), G, a.tw, tid, nthr);
+        fft_fixed<LF, false, false, FP, 1, -2, true>(reinterpret_cast<C*>(smraw), G, tws, tid, nthr);
       } else {
         fft_smem<false, false, (LF < 0)>(reinterpret_cast<C*>(smraw), pitch, 1, 3, G, plan.L, plan.nstage, plan.packed, a.tw,
                                tid, nthr);
