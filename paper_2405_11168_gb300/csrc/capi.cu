@@ -1403,7 +1403,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
   c->nthr_y = col_threads(c->n2);
   c->nthr_z = col_threads(c->n3);
   const size_t cs = c->f64 ? 16 : 8;
-  c->smem_y = (size_t)c->n2 * 3 * c->ct * cs;
+  // a tile, then (fixed lengths) the twiddle table 16 bytes behind it
+  c->smem_y = (size_t)c->n2 * 3 * c->ct * cs + 16 + (size_t)c->n2 * cs;
   // the z pass may load its tile by a tensor copy: room for its alignment and barrier
   c->smem_z = (size_t)c->n3 * 3 * c->ct * cs + hs::kColpTmaSlack + (size_t)c->n3 * cs;
   c->xfuse = (o.xfuse == 1);

@@ -78,6 +78,17 @@ __device__ __forceinline__ void green_core(const ColArgs<T>& a, T c0a, T c0b, bo
                                            typename cplx_t<T>::type xz, typename cplx_t<T>::type (&F)[3],
                                            typename cplx_t<T>::type (&U)[3]);
 
+// The Green update's arithmetic with every rounding spelled out (a product rounded on its own,
+// or fused into one FMA), so that its results do not depend on how the compiler contracts the
+// expressions in the kernel it is inlined into: every column-pass variant gives the same bits.
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+__device__ __forceinline__ float fma_rn(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+__device__ __forceinline__ double fma_rn(double x, double y, double z) { return __fma_rn(x, y, z); }
+template <typename C> __device__ __forceinline__ C cmul_rn(C p, C q) {
+  return cmk<C>(fma_rn(p.x, q.x, -mul_rn(p.y, q.y)), fma_rn(p.x, q.y, mul_rn(p.y, q.x)));
+}
+
 template <typename T>
 __device__ __forceinline__ void green_apply(const ColArgs<T>& a, T c0a, T c0b, bool c0iso, int h1, int h2, int h3,
                                             typename cplx_t<T>::type (&F)[3],
@@ -91,7 +102,7 @@ __device__ __forceinline__ void green_apply(const ColArgs<T>& a, T c0a, T c0b, b
     return;
   }
   const C ex = __ldg(a.tw1 + h1), ey = __ldg(a.tw2 + h2), ez = __ldg(a.tw3 + h3);
-  green_core<T>(a, c0a, c0b, c0iso, cmul(ey, ez), cmul(ex, ey), cmul(ex, ez), F, U);
+  green_core<T>(a, c0a, c0b, c0iso, cmul_rn(ey, ez), cmul_rn(ex, ey), cmul_rn(ex, ez), F, U);
 }
 
 // The update at one q from the products of the per-axis phase factors exp(-i q_y) exp(-i q_z)
@@ -110,45 +121,47 @@ __device__ __forceinline__ void green_core(const ColArgs<T>& a, T c0a, T c0b, bo
   // 2 M in Voigt pair order (11,22,33,23,13,12), M_ik = 2 Re(D_i conj D_k); the factors of two
   // are powers of two, so folding them into the constants below changes no rounding
   T M[6];
-  M[0] = D[0].x * D[0].x + D[0].y * D[0].y;
-  M[1] = D[1].x * D[1].x + D[1].y * D[1].y;
-  M[2] = D[2].x * D[2].x + D[2].y * D[2].y;
-  M[3] = D[1].x * D[2].x + D[1].y * D[2].y;
-  M[4] = D[0].x * D[2].x + D[0].y * D[2].y;
-  M[5] = D[0].x * D[1].x + D[0].y * D[1].y;
+  M[0] = fma_rn(D[0].x, D[0].x, mul_rn(D[0].y, D[0].y));
+  M[1] = fma_rn(D[1].x, D[1].x, mul_rn(D[1].y, D[1].y));
+  M[2] = fma_rn(D[2].x, D[2].x, mul_rn(D[2].y, D[2].y));
+  M[3] = fma_rn(D[1].x, D[2].x, mul_rn(D[1].y, D[2].y));
+  M[4] = fma_rn(D[0].x, D[2].x, mul_rn(D[0].y, D[2].y));
+  M[5] = fma_rn(D[0].x, D[1].x, mul_rn(D[0].y, D[1].y));
   T A[6];
   if (c0iso) {
     // Omega^-1_jl = sum_ik lambda0_jikl M_ik = (lambda0 + mu0) M_jl + mu0 tr(M) delta_jl
-    const T tr = (T(0.5) * c0b) * (M[0] + M[1] + M[2]);
+    const T tr = mul_rn(T(0.5) * c0b, (M[0] + M[1] + M[2]));
     const T ca = T(0.5) * c0a;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) A[i] = ca * M[i] + (i < 3 ? tr : T(0));
+    for (int i = 0; i < 6; ++i) A[i] = i < 3 ? fma_rn(ca, M[i], tr) : mul_rn(ca, M[i]);
   } else {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      T s = 0;
+      T s = mul_rn(a.G6[i * 6], M[0]);
 #pragma unroll
-      for (int j = 0; j < 6; ++j) s += a.G6[i * 6 + j] * M[j];
+      for (int j = 1; j < 6; ++j) s = fma_rn(a.G6[i * 6 + j], M[j], s);
       A[i] = T(0.5) * s;
     }
   }
   // inverse of the symmetric 3x3 [[A0,A5,A4],[A5,A1,A3],[A4,A3,A2]]
-  const T c11 = A[1] * A[2] - A[3] * A[3];
-  const T c22 = A[0] * A[2] - A[4] * A[4];
-  const T c33 = A[0] * A[1] - A[5] * A[5];
-  const T c23 = A[4] * A[5] - A[0] * A[3];
-  const T c13 = A[5] * A[3] - A[1] * A[4];
-  const T c12 = A[4] * A[3] - A[2] * A[5];
-  const T det = A[0] * c11 + A[5] * c12 + A[4] * c13;
+  const T c11 = fma_rn(A[1], A[2], -mul_rn(A[3], A[3]));
+  const T c22 = fma_rn(A[0], A[2], -mul_rn(A[4], A[4]));
+  const T c33 = fma_rn(A[0], A[1], -mul_rn(A[5], A[5]));
+  const T c23 = fma_rn(A[4], A[5], -mul_rn(A[0], A[3]));
+  const T c13 = fma_rn(A[5], A[3], -mul_rn(A[1], A[4]));
+  const T c12 = fma_rn(A[4], A[3], -mul_rn(A[2], A[5]));
+  const T det = fma_rn(A[4], c13, fma_rn(A[5], c12, mul_rn(A[0], c11)));
   const T s = a.scale / det;
-  const T O[3][3] = {{c11 * s, c12 * s, c13 * s}, {c12 * s, c22 * s, c23 * s}, {c13 * s, c23 * s, c33 * s}};
+  const T O[3][3] = {{mul_rn(c11, s), mul_rn(c12, s), mul_rn(c13, s)},
+                     {mul_rn(c12, s), mul_rn(c22, s), mul_rn(c23, s)},
+                     {mul_rn(c13, s), mul_rn(c23, s), mul_rn(c33, s)}};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     C acc = U[j];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      acc.x -= O[j][k] * F[k].x;
-      acc.y -= O[j][k] * F[k].y;
+      acc.x = fma_rn(-O[j][k], F[k].x, acc.x);
+      acc.y = fma_rn(-O[j][k], F[k].y, acc.y);
     }
     U[j] = acc;
   }
@@ -208,10 +221,12 @@ __device__ __forceinline__ void col_green(const ColArgs<T>& a, typename cplx_t<T
 // column tid % CT and walks z = tid / CT, tid / CT + NT / CT, ..., so exp(-i q_x), its product
 // with the block's exp(-i q_y), the state address of its column and whether its (q_x, q_y) can
 // be a translation mode are set once; per point only exp(-i q_z) and two products remain.
+// tz: a shared-memory copy of the z pass's twiddle table, which holds the z phase factors
+// (the same values as tw3).
 template <typename T, int CT, int L, int NT>
 __device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cplx_t<T>::type* sm, size_t base,
                                                 size_t rstride, size_t cstride, int x0, int outer, int ncol,
-                                                int tid) {
+                                                int tid, const typename cplx_t<T>::type* tz) {
   using C = typename cplx_t<T>::type;
   static_assert(NT % CT == 0 && (L * CT) % NT == 0, "whole columns per thread");
   constexpr int W = 3 * CT;
@@ -225,7 +240,7 @@ __device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cp
   const T c0b = a.c0dev != nullptr ? a.c0dev[1] : a.c0b;
   const int h1 = x0 + col, h2 = outer;
   const C ex = __ldg(a.tw1 + h1), ey = __ldg(a.tw2 + h2);
-  const C xy = cmul(ex, ey);
+  const C xy = cmul_rn(ex, ey);
   // translation modes q = 0 and (pi, pi, pi): only where (q_x, q_y) is (0, 0) or (pi, pi)
   const int ztrans = (h1 == 0 && h2 == 0) ? 0 : ((2 * h1 == a.n1 && 2 * h2 == a.n2) ? a.n3 / 2 : -1);
   C* Sc = a.S + base + col;
@@ -248,8 +263,8 @@ __device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cp
 #pragma unroll
         for (int c = 0; c < 3; ++c) U[u][c] = cmk<C>(0, 0);
       } else {
-        const C ez = __ldg(a.tw3 + z);
-        green_core<T>(a, c0a, c0b, c0iso, cmul(ey, ez), xy, cmul(ex, ez), F, U[u]);
+        const C ez = tw_load<true>(tz, z);
+        green_core<T>(a, c0a, c0b, c0iso, cmul_rn(ey, ez), xy, cmul_rn(ex, ez), F, U[u]);
       }
       const size_t g = (size_t)z * rstride;
 #pragma unroll
@@ -296,6 +311,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
   // flight at once); columns past the row pitch are zero
   constexpr int EPC = 16 / (int)sizeof(C);  // complex values per 16-byte chunk
   constexpr int CPR = CT / EPC;             // chunks per (row, component)
+  // fixed lengths: the transforms (and the Green step's z phases) read the twiddle table from a
+  // copy in shared memory, 16 bytes behind the tile (and the state tile, when there is one); the
+  // host adds 16 + L complex values to the tile's shared memory for it
+  C* const tws = reinterpret_cast<C*>(
+      smb + (size_t)((MODE == COL_Z_GREEN && a.state_smem) ? 2 : 1) * L * W * sizeof(C) + 16);
   if constexpr (TMA) {
     uint64_t* const tbar = reinterpret_cast<uint64_t*>(smb + (size_t)L * W * sizeof(C));
     // the copy needs a 128-byte aligned destination and a 64-byte aligned map: checked once,
@@ -316,9 +336,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
       const int e = i / 3, c = i - 3 * e;
       asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
     }
-    // the transforms' twiddle table, copied behind the tile's barrier
-    C* const tws = reinterpret_cast<C*>(smb + (size_t)L * W * sizeof(C) + 16);
-    for (int i = tid; i < L; i += nthr) tws[i] = __ldg(tw + i);
+    for (int i = tid; LF > 0 && i < L; i += nthr) tws[i] = __ldg(tw + i);
     __syncthreads();  // the barrier is initialised before anyone waits on it
     if (!mbar_wait(tbar, 0)) {
       if (tid == 0) a.st->done = DONE_TIMEOUT;
@@ -361,6 +379,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
   } else {
     cp_async_wait_all();
   }
+  for (int i = tid; !TMA && LF > 0 && i < L; i += nthr) tws[i] = __ldg(tw + i);
   __syncthreads();
   if constexpr (LF > 0) {
     // compile-time plan; the last stage writes straight to global memory
@@ -371,23 +390,23 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
     io.rstride = rstride;
     io.ccols = ccols;
     io.ncol = ncol;
-    const C* const twf = TMA ? reinterpret_cast<const C*>(smb + (size_t)L * W * sizeof(C) + 16) : tw;
     if (MODE == COL_Z_GREEN) {
-      fft_col_fixed<LF, W, CT, false, false, false, TMA>(sm, io, twf, tid, nthr);
+      fft_col_fixed<LF, W, CT, false, false, false, true>(sm, io, tws, tid, nthr);
       if (ss != nullptr) {
         cp_async_wait_all();
         __syncthreads();
       }
       if constexpr (NT > 0 && NT % CT == 0 && (LF * CT) % NT == 0) {
-        if (ss == nullptr) col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, ncol, tid);
+        if (ss == nullptr) col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, ncol, tid, tws);
         else col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
       } else {
         col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
       }
       __syncthreads();
-      fft_col_fixed<LF, W, CT, true, false, true, TMA>(sm, io, twf, tid, nthr);
+      fft_col_fixed<LF, W, CT, true, false, true, true>(sm, io, tws, tid, nthr);
     } else {
-      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, false, true>(sm, io, tw, tid, nthr);
+      fft_col_fixed<LF, W, CT, MODE == COL_Y_INV || MODE == COL_Z_INV_STATE, false, true, true>(sm, io, tws, tid,
+                                                                                            nthr);
     }
     return;
   }
@@ -529,7 +548,7 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     if (MODE == COL_Z_GREEN) {
       fft_col_fixed<LF, W, CT, false, false, false, true>(sm, io, tws, tid, NT);
       if constexpr (NT % CT == 0 && (LF * CT) % NT == 0) {
-        col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, io.ncol, tid);
+        col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, io.ncol, tid, tws);
       } else {
         col_green<T, CT>(a, sm, nullptr, base, rstride, cstride, x0, outer, io.ncol, L, tid, NT);
       }

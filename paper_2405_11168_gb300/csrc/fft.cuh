@@ -345,11 +345,7 @@ template <int NS, int R> __device__ __forceinline__ int stockham_out(int b) {
 // of the table in shared memory
 template <bool TWS, typename C> __device__ __forceinline__ C tw_load(const C* __restrict__ tw, int i) {
   if constexpr (TWS) {
-    C w;
-    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(tw + i));
-    if constexpr (sizeof(C) == 8) asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(w.x), "=f"(w.y) : "r"(a));
-    else asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(w.x), "=d"(w.y) : "r"(a));
-    return w;
+    return tw[i];
   } else {
     return __ldg(tw + i);
   }
