@@ -1406,7 +1406,7 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
   // a tile, then (fixed lengths) the twiddle table 16 bytes behind it
   c->smem_y = (size_t)c->n2 * 3 * c->ct * cs + 16 + (size_t)c->n2 * cs;
   // the z pass may load its tile by a tensor copy: room for its alignment and barrier
-  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs + hs::kColpTmaSlack + (size_t)c->n3 * cs;
+  c->smem_z = (size_t)c->n3 * 3 * c->ct * cs + hs::kColpTmaSlack + 2 * (size_t)c->n3 * cs;
   c->xfuse = (o.xfuse == 1);
   {
     // radix-5/7/11 lengths run the split path with the default column tile only
@@ -1533,8 +1533,8 @@ static hs_status create_impl(hs_ctx** out, const int grid[3], const hs_material*
       if (L != 128 && L != 256 && L != 512) continue;
       if (axis == 2 && c->zstate_smem) continue;  // the persistent z pass reads the state point by point
       // the tiles may arrive by tensor copies: room for their alignment and barriers
-      // and for the twiddle table behind them
-      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + hs::kColpTmaSlack + (size_t)L * cs;
+      // and for the twiddle tables behind them
+      const size_t smem = 2 * (size_t)L * 3 * c->ct * cs + hs::kColpTmaSlack + 2 * (size_t)L * cs;
       if (smem > (size_t)smem_optin) continue;
       const int nthr = axis == 1 ? c->nthr_y : c->nthr_z;
       int per_sm = 0;

@@ -311,11 +311,20 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
   // flight at once); columns past the row pitch are zero
   constexpr int EPC = 16 / (int)sizeof(C);  // complex values per 16-byte chunk
   constexpr int CPR = CT / EPC;             // chunks per (row, component)
-  // fixed lengths: the transforms (and the Green step's z phases) read the twiddle table from a
-  // copy in shared memory, 16 bytes behind the tile (and the state tile, when there is one); the
-  // host adds 16 + L complex values to the tile's shared memory for it
+  // fixed lengths: the transforms read their twiddles from the plan's per-stage table in shared
+  // memory, 16 bytes behind the tile (and the state tile, when there is one), and the Green step
+  // its z phases from a plain copy of the table after it; the host adds 16 + 2 L complex values
+  // to the tile's shared memory for them
   C* const tws = reinterpret_cast<C*>(
       smb + (size_t)((MODE == COL_Z_GREEN && a.state_smem) ? 2 : 1) * L * W * sizeof(C) + 16);
+  C* const tzs = tws + L;
+  auto copy_tables = [&]() {
+    if constexpr (LF > 0) {
+      stage_twiddles<LF>(tws, tw, tid, nthr);
+      if (MODE == COL_Z_GREEN)
+        for (int i = tid; i < L; i += nthr) tzs[i] = __ldg(tw + i);
+    }
+  };
   if constexpr (TMA) {
     uint64_t* const tbar = reinterpret_cast<uint64_t*>(smb + (size_t)L * W * sizeof(C));
     // the copy needs a 128-byte aligned destination and a 64-byte aligned map: checked once,
@@ -336,7 +345,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
       const int e = i / 3, c = i - 3 * e;
       asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.S + c * cstride + base + e * rstride));
     }
-    for (int i = tid; LF > 0 && i < L; i += nthr) tws[i] = __ldg(tw + i);
+    copy_tables();
     __syncthreads();  // the barrier is initialised before anyone waits on it
     if (!mbar_wait(tbar, 0)) {
       if (tid == 0) a.st->done = DONE_TIMEOUT;
@@ -379,7 +388,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
   } else {
     cp_async_wait_all();
   }
-  for (int i = tid; !TMA && LF > 0 && i < L; i += nthr) tws[i] = __ldg(tw + i);
+  if (!TMA) copy_tables();
   __syncthreads();
   if constexpr (LF > 0) {
     // compile-time plan; the last stage writes straight to global memory
@@ -397,7 +406,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_col(const __grid
         __syncthreads();
       }
       if constexpr (NT > 0 && NT % CT == 0 && (LF * CT) % NT == 0) {
-        if (ss == nullptr) col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, ncol, tid, tws);
+        if (ss == nullptr) col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, ncol, tid, tzs);
         else col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
       } else {
         col_green<T, CT>(a, sm, ss, base, rstride, cstride, x0, outer, ncol, L, tid, nthr);
@@ -505,9 +514,13 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
       else tma_load_5d(sm + (size_t)h * 256 * W, &a_.tmap, 2 * x0, 0, outer, h * 256, (int)blockIdx.z, &tbar[b]);
     }
   };
-  // the transforms' twiddle table, copied behind the barriers (read after the first barrier)
+  // the plan's per-stage twiddle table behind the barriers, then (z pass) a plain copy of the table
+  // for the Green step's z phases (read after the first barrier)
   C* const tws = reinterpret_cast<C*>(smb + (size_t)2 * L * W * sizeof(C) + 16);
-  for (int i = tid; i < L; i += NT) tws[i] = __ldg(a.tw + i);
+  C* const tzs = tws + L;
+  stage_twiddles<LF>(tws, a.tw, tid, NT);
+  if (MODE == COL_Z_GREEN)
+    for (int i = tid; i < L; i += NT) tzs[i] = __ldg(a.tw + i);
   bool timed_out = false;
   int t = blockIdx.x;
   if constexpr (TMA) {
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(NT, 2) k_colp(const __grid_constant__ ColArgs<
     if (MODE == COL_Z_GREEN) {
       fft_col_fixed<LF, W, CT, false, false, false, true>(sm, io, tws, tid, NT);
       if constexpr (NT % CT == 0 && (LF * CT) % NT == 0) {
-        col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, io.ncol, tid, tws);
+        col_green_fixed<T, CT, LF, NT>(a, sm, base, rstride, cstride, x0, outer, io.ncol, tid, tzs);
       } else {
         col_green<T, CT>(a, sm, nullptr, base, rstride, cstride, x0, outer, io.ncol, L, tid, NT);
       }

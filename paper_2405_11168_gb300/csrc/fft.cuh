@@ -341,6 +341,33 @@ template <int NS, int R> __device__ __forceinline__ int stockham_out(int b) {
   return ((b >> ilog2_c(NS)) << (ilog2_c(NS) + ilog2_c(R))) | (b & (NS - 1));
 }
 
+// Twiddle table of a fixed plan in shared memory, laid out per stage: stage s (NS_s = r_0 ... r_{s-1}
+// > 1) needs w_L^{kk m step_s} for m = 1 .. R_s - 1 and kk < NS_s, kept at entry
+// NS_s - r_0 + (m - 1) NS_s + kk.  The lanes of a warp hold consecutive kk, so they read consecutive
+// entries (no bank conflicts); since (R_s - 1) NS_s = NS_{s+1} - NS_s the stages follow each other
+// and the table has L - r_0 entries.
+template <int L, typename C>
+__device__ __forceinline__ void stage_twiddles(C* tab, const C* __restrict__ tw, int tid, int nthr) {
+  constexpr int R0 = FixedPlan<L>::r(0);
+  for (int j = tid; j < L - R0; j += nthr) {
+    int ns = R0, st = 1;
+    while (st + 1 < FixedPlan<L>::n && j >= ns * FixedPlan<L>::r(st) - R0) {
+      ns *= FixedPlan<L>::r(st);
+      ++st;
+    }
+    const int i = j - (ns - R0);
+    const int m = i / ns + 1, kk = i - (m - 1) * ns;
+    tab[j] = __ldg(tw + kk * m * (L / (ns * FixedPlan<L>::r(st))));
+  }
+}
+// twiddle m of butterfly kk in the stage with NS and step: from the per-stage table in shared
+// memory (TWS), or from the plain table through the read-only path
+template <bool TWS, int L, int NS, typename C>
+__device__ __forceinline__ C stage_tw(const C* __restrict__ tw, int m, int kk, int step) {
+  if constexpr (TWS) return tw[(NS - FixedPlan<L>::r(0)) + (m - 1) * NS + kk];
+  else return __ldg(tw + kk * m * step);
+}
+
 // twiddle i of the table: from global memory through the read-only path, or (TWS) from a copy
 // of the table in shared memory
 template <bool TWS, typename C> __device__ __forceinline__ C tw_load(const C* __restrict__ tw, int i) {
@@ -388,7 +415,7 @@ __device__ __forceinline__ void stage_fixed(C* buf, int s, int t, bool active, c
       if (NS > 1) {
 #pragma unroll
         for (int m = 1; m < R; ++m) {
-          C w = tw_load<TWS>(tw, kk * m * step);
+          C w = stage_tw<TWS, L, NS>(tw, m, kk, step);
           if (INV) w.y = -w.y;
           v[k][m] = cmul(v[k][m], w);
         }
@@ -417,7 +444,7 @@ __device__ __forceinline__ void stages_fixed(C* buf, int s, int t, bool active, 
 }
 
 // Same contract as fft_smem with L, the strides and the mapping fixed at compile time.  TWS: tw
-// points to a copy of the twiddle table in shared memory.
+// points to the plan's per-stage twiddle table in shared memory (stage_twiddles).
 template <int L, bool INV, bool COLMAP, int SS, int ES, int PS, bool TWS = false, typename C>
 __device__ __forceinline__ void fft_fixed(C* buf, int nseq, const C* __restrict__ tw, int tid, int nthreads) {
   constexpr int T = L / kE;
@@ -486,7 +513,7 @@ __device__ __forceinline__ void stage_col(C* sm, const ColIO<C>& io, int s, int 
       if (NS > 1) {
 #pragma unroll
         for (int m = 1; m < R; ++m) {
-          C w = tw_load<TWS>(tw, kk * m * step);
+          C w = stage_tw<TWS, L, NS>(tw, m, kk, step);
           if (INV) w.y = -w.y;
           v[k][m] = cmul(v[k][m], w);
         }
@@ -520,7 +547,7 @@ __device__ __forceinline__ void stages_col(C* sm, const ColIO<C>& io, int s, int
 }
 
 // FFT of the W = 3 * CT columns of a tile; lanes walk across columns (COLMAP).
-// TWS: tw points to a copy of the twiddle table in shared memory.
+// TWS: tw points to the plan's per-stage twiddle table in shared memory (stage_twiddles).
 template <int L, int W, int CT, bool INV, bool IN_G, bool OUT_G, bool TWS = false, typename C>
 __device__ __forceinline__ void fft_col_fixed(C* sm, const ColIO<C>& io, const C* __restrict__ tw, int tid,
                                               int nthreads) {

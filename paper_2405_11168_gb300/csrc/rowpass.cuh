@@ -63,7 +63,7 @@ struct RowLayout {
   size_t outbytes;  // bytes of one output row (C2R: n1 real; R2C: P complex)
   size_t stage;     // bytes of one staging buffer
   size_t bar;       // two mbarriers of the staging buffers (bulk-copy loads)
-  size_t tws;       // the twiddle table (n1 complex values; fixed lengths)
+  size_t tws;       // the per-stage twiddle table (fewer than n1 complex values; fixed lengths)
   size_t total;
 };
 __host__ __device__ inline RowLayout row_layout(int mode, int n1, int P, int nthr, int tsize) {
@@ -173,12 +173,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_row(const RowAr
     }
     __syncthreads();
   }
-  // fixed lengths: the transforms read the twiddle table from a copy in shared memory (first read
-  // after the barrier that opens the first batch)
+  // fixed lengths: the transforms read their twiddles from the plan's per-stage table in shared
+  // memory (first read after the barrier that opens the first batch)
   C* const tws = reinterpret_cast<C*>(smraw + L.tws);
-  if constexpr (LF > 0) {
-    for (int i = tid; i < n1; i += nthr) tws[i] = __ldg(a.tw + i);
-  }
+  if constexpr (LF > 0) stage_twiddles<LF>(tws, a.tw, tid, nthr);
   int buf = 0;
   if ((int)blockIdx.x < nbatch && (!bload || tid == 0)) row_stage<T, MODE>(a, L, smraw, blockIdx.x, 0, bload);
   int k = 0;
