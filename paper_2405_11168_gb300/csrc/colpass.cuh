@@ -232,7 +232,10 @@ __device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cp
   constexpr int W = 3 * CT;
   constexpr int ZS = NT / CT;        // z step of a thread
   constexpr int NPT = L * CT / NT;   // points per thread
-  constexpr int GU = NPT < 4 ? NPT : 4;
+  // points in groups of GU; the state loads of the next group are issued before the update of
+  // the current one (different points), so their latency runs under its arithmetic
+  constexpr int GU = NPT < 2 ? NPT : 2;
+  static_assert(NPT % GU == 0, "whole groups per thread");
   const int col = tid % CT, zt = tid / CT;
   if (col >= ncol) return;
   const bool c0iso = a.c0iso || a.c0dev != nullptr;
@@ -244,15 +247,24 @@ __device__ __forceinline__ void col_green_fixed(const ColArgs<T>& a, typename cp
   // translation modes q = 0 and (pi, pi, pi): only where (q_x, q_y) is (0, 0) or (pi, pi)
   const int ztrans = (h1 == 0 && h2 == 0) ? 0 : ((2 * h1 == a.n1 && 2 * h2 == a.n2) ? a.n3 / 2 : -1);
   C* Sc = a.S + base + col;
-#pragma unroll
-  for (int u0 = 0; u0 < NPT; u0 += GU) {
-    C U[GU][3];
+  auto load_group = [&](C (&V)[GU][3], int u0) {
 #pragma unroll
     for (int u = 0; u < GU; ++u) {
       const size_t g = (size_t)(zt + (u0 + u) * ZS) * rstride;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) U[u][c] = Sc[c * cstride + g];
+      for (int c = 0; c < 3; ++c) V[u][c] = Sc[c * cstride + g];
     }
+  };
+  C Un[GU][3];
+  load_group(Un, 0);
+#pragma unroll
+  for (int u0 = 0; u0 < NPT; u0 += GU) {
+    C U[GU][3];
+#pragma unroll
+    for (int u = 0; u < GU; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) U[u][c] = Un[u][c];
+    if (u0 + GU < NPT) load_group(Un, u0 + GU);
 #pragma unroll
     for (int u = 0; u < GU; ++u) {
       const int z = zt + (u0 + u) * ZS;
