@@ -275,6 +275,29 @@ def test_column_tensor_copies_match_cp_async(hs, prec, grid):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("grid", [(24, 64, 256), (20, 48, 40)])
+def test_state_tile_in_shared_memory_matches_point_reads(hs, prec, grid):
+    """The z pass that copies the state tile to shared memory beside the force tile (col_state 2,
+    the generic Green loop) gives bit-identical iterates, fields and errors to the one that reads
+    the state point by point (col_state 1), at a compile-time z length (256) and a run-time one
+    (40): the Green arithmetic spells out every rounding, so neither variant depends on how the
+    compiler contracts it."""
+    ids = synth.random_phase_map(tuple(grid), 2, seed=11)
+    table = synth.two_phase_table(1.0, 0.3, 8.0, 0.3)
+    runs = []
+    for state in (1, 2):
+        s = hs.Solver(ids, table, precision=prec, col_state=state, inner_max=8)
+        out = s.solve(E_MIX, tol=1e-9, max_iter=30)
+        runs.append((out["iters"], out["err"], out["sig_eff"].copy(), out["eps"].cpu().numpy(),
+                     out["sig"].cpu().numpy(), s.err_history().copy()))
+        s.close()
+    a, b = runs
+    assert a[0] == b[0] and a[1] == b[1]
+    for i in (2, 3, 4, 5):
+        np.testing.assert_array_equal(a[i], b[i])
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_graph_replay_matches_plain_launches(hs, prec):
     """Iteration chunks replayed as captured CUDA graphs give bit-identical iterates,
     fields and errors to plain launches, across solves with different loads and after
