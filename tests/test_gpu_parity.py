@@ -256,12 +256,14 @@ def test_column_tensor_copies_match_cp_async(hs, prec, grid):
     512, the latter in two copies per tile; z passes of length 64, 256 and 128, one tile per
     block or persistent) give bit-identical iterates, fields and errors to the 16-byte cp.async
     loads, in FP64, FP32 and refined mode, with ragged x tiles (the last tile of 8 or 4 columns
-    partly past the row pitch, filled with zeros by the copy)."""
+    partly past the row pitch, filled with zeros by the copy); so do y passes with one tile per
+    block instead of persistent blocks."""
     ids = synth.random_phase_map(tuple(grid), 2, seed=7)
     table = synth.two_phase_table(1.0, 0.3, 6.0, 0.3)
     runs = []
-    # cp.async loads; tensor copies; tensor copies with a persistent z pass (z lengths 128, 256)
-    for copy, pipe in ((1, 0), (2, 0), (2, 2)):
+    # cp.async loads; tensor copies; tensor copies with a persistent z pass (z lengths 128, 256);
+    # one tile per block in the y passes as well
+    for copy, pipe in ((1, 0), (2, 0), (2, 2), (1, 1)):
         s = hs.Solver(ids, table, precision=prec, col_copy=copy, col_pipe=pipe, inner_max=8)
         out = s.solve(E_MIX, tol=1e-9, max_iter=30)
         runs.append((out["iters"], out["err"], out["sig_eff"].copy(), out["eps"].cpu().numpy(),
